@@ -1,0 +1,113 @@
+"""Seeded synthetic inputs: packed Bernoulli(0.5) bit-vectors.
+
+This module holds no arithmetic of the hashing method. It only draws the
+keys and Toeplitz seeds that both the CUDA path and the CPU oracle consume.
+Reconciled QKD keys are modelled as i.i.d. Bernoulli(0.5) bits (the paper's
+input X_n of Section 2.3 and the n+r-1 random bits of the Toeplitz
+description of Section 2.2).
+
+Generator: SplitMix64 (G. Steele, D. Lea, C. Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014; constants as in S. Vigna's
+public-domain reference). It is counter based: word ``w`` of a stream is
+``mix(state0 + (w + 1) * GAMMA)``, so any slice can be drawn independently.
+
+Stream convention: ``state0 = mix(base_seed ^ (stream_id * GAMMA))``.
+Stream 0 is the key and stream 1 the seed of a single block; batched keys use
+streams 2, 3, ...; block ``b`` of an uneven batch uses streams 2b+2 (key) and
+2b+3 (seed).
+
+Packed layout: bit ``j`` of a bit-vector lives in 64-bit word ``j // 64`` at
+bit position ``j % 64`` (LSB first); bits at or past the vector's length in
+the last word are zero.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+STREAM_KEY = 0
+STREAM_SEED = 1
+
+
+def _mix(z: np.ndarray) -> np.ndarray:
+    """SplitMix64 output function (variant 13 of Stafford's mixers)."""
+    z = np.asarray(z, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+    return z ^ (z >> np.uint64(31))
+
+
+def stream_state(base_seed: int, stream_id: int) -> np.uint64:
+    with np.errstate(over="ignore"):
+        s = np.uint64(base_seed & 0xFFFFFFFFFFFFFFFF) ^ (np.uint64(stream_id) * GAMMA)
+    return _mix(np.array([s], dtype=np.uint64))[0]
+
+
+def words(base_seed: int, stream_id: int, nwords: int, offset: int = 0) -> np.ndarray:
+    """``nwords`` raw 64-bit words of one stream, starting at word ``offset``."""
+    s0 = stream_state(base_seed, stream_id)
+    idx = np.arange(offset + 1, offset + nwords + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        return _mix(s0 + idx * GAMMA)
+
+
+def nwords_for(nbits: int) -> int:
+    return (nbits + 63) // 64
+
+
+def mask_tail(w: np.ndarray, nbits: int) -> np.ndarray:
+    """Zero the bits at positions >= nbits (in place on a copy)."""
+    w = np.array(w, dtype=np.uint64, copy=True)
+    nw = nwords_for(nbits)
+    w[nw:] = 0
+    r = nbits % 64
+    if r and nw:
+        w[nw - 1] &= np.uint64((1 << r) - 1)
+    return w
+
+
+def bernoulli_bits(base_seed: int, stream_id: int, nbits: int) -> np.ndarray:
+    """Packed i.i.d. Bernoulli(0.5) bit-vector of ``nbits`` bits."""
+    return mask_tail(words(base_seed, stream_id, nwords_for(nbits)), nbits)
+
+
+def block_inputs(n: int, m: int, base_seed: int = 0, key_stream: int = STREAM_KEY,
+                 seed_stream: int = STREAM_SEED):
+    """(key, seed) packed words for one block: n key bits, n+m-1 seed bits."""
+    return (bernoulli_bits(base_seed, key_stream, n),
+            bernoulli_bits(base_seed, seed_stream, n + m - 1))
+
+
+def batch_keys(n: int, nkeys: int, base_seed: int = 0, first_stream: int = 2) -> np.ndarray:
+    """(nkeys, ceil(n/64)) packed keys, key k drawn from stream first_stream+k."""
+    nw = nwords_for(n)
+    out = np.empty((nkeys, nw), dtype=np.uint64)
+    for k in range(nkeys):
+        out[k] = bernoulli_bits(base_seed, first_stream + k, n)
+    return out
+
+
+def unpack(words_: np.ndarray, nbits: int) -> np.ndarray:
+    """Packed words -> uint8 array of nbits bits (LSB first)."""
+    b = np.unpackbits(np.ascontiguousarray(words_, dtype="<u8").view(np.uint8), bitorder="little")
+    return b[:nbits].copy()
+
+
+def pack(bits: np.ndarray) -> np.ndarray:
+    """uint8/bool bit array -> packed uint64 words (tail zero)."""
+    bits = np.asarray(bits, dtype=np.uint8) & 1
+    nb = bits.size
+    nw = nwords_for(nb)
+    padded = np.zeros(nw * 64, dtype=np.uint8)
+    padded[:nb] = bits
+    return np.packbits(padded, bitorder="little").view("<u8").astype(np.uint64)
+
+
+def uniform01(base_seed: int, stream_id: int, count: int) -> np.ndarray:
+    """``count`` doubles in [0, 1) from the top 53 bits of a stream."""
+    w = words(base_seed, stream_id, count)
+    return (w >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
