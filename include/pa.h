@@ -1,0 +1,160 @@
+/*
+ * pa.h -- C ABI of the GB300 Toeplitz-hash privacy-amplification library (libpa.so).
+ *
+ * The library computes the privacy-amplification hash of the paper's Section 2.2:
+ * an m x n binary Toeplitz matrix T, fixed by an (n+m-1)-bit seed s, compresses an
+ * n-bit reconciled key x into the m-bit final key
+ *
+ *     y = T x mod 2,   T[i][j] = s[i - j + n - 1]   (0 <= i < m, 0 <= j < n),
+ *
+ * evaluated, as in Eq. 4, as a linear convolution of s and x through a cyclic
+ * convolution of length L >= n+m-1 computed with FFTs (forward transform,
+ * pointwise product with the seed's spectrum, inverse transform, rounding,
+ * mod 2). All arithmetic runs in the library's own CUDA kernels on one GPU.
+ *
+ * Bit layout (every bit-vector argument): bit j is bit (j % 64) of 64-bit word
+ * j / 64, little-endian words. A key occupies ceil(n/64) words, a seed
+ * ceil((n+m-1)/64) words, a final key ceil(m/64) words. Input bits past the
+ * vector's length are ignored; output bits at positions >= m are written as 0.
+ *
+ * Errors: every entry point returns an int, PA_OK (0) on success or one of the
+ * negative PA_E* codes below; pa_strerror() names them. No C++ exception crosses
+ * this boundary. Device pointers must be 16-byte aligned.
+ *
+ * Threads: a plan may be used from one host thread at a time; calls on one plan
+ * must be issued to one stream at a time. A server is thread-safe.
+ */
+#ifndef PA_H_
+#define PA_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream handle (the same object as cudaStream_t); NULL is the legacy default stream. */
+typedef struct CUstream_st *pa_stream_t;
+
+/* Error codes. */
+#define PA_OK 0
+#define PA_EINVAL (-1)       /* bad size, null or misaligned pointer, seed length mismatch, bad handle */
+#define PA_ENOMEM (-2)       /* device or pinned-host allocation failed */
+#define PA_EAGAIN (-3)       /* server: admission cap reached and queue full, retry later */
+#define PA_EPENDING (-4)     /* server: the ticket has not completed yet */
+#define PA_ETIMEOUT (-5)     /* a bounded wait expired */
+#define PA_EPRECISION (-6)   /* no precision mode produced an unambiguous rounding (should not happen) */
+#define PA_ECUDA (-7)        /* a CUDA runtime call failed; see pa_last_cuda_error() */
+#define PA_ENOSEED (-8)      /* pa_hash_batch before pa_set_seed */
+#define PA_EUNSUPPORTED (-9) /* size or mode this build does not handle */
+
+/*
+ * Arithmetic of the transform (paper Section 5 names the precision of the FFT
+ * as the open question; these are the three answers the library offers).
+ *   PA_FP64        double-precision complex FFTs.
+ *   PA_FP32_GUARD  single-precision complex FFTs; every key's rounding margin
+ *                  max_i |v_i - rint(v_i)| is checked, and a key whose margin
+ *                  exceeds 0.25 is recomputed in FP64.
+ *   PA_NTT64       exact number-theoretic transform modulo p = 2^64 - 2^32 + 1.
+ * The output bits are the same in every mode.
+ */
+typedef enum { PA_FP64 = 0, PA_FP32_GUARD = 1, PA_NTT64 = 2 } pa_dtype_t;
+
+typedef struct pa_plan pa_plan_t;
+
+/* Per-key diagnostics filled by pa_hash_batch when the caller passes one. */
+typedef struct {
+    float *margin;       /* host array of nkeys, or NULL: rounding margin of the mode that produced each key */
+    int32_t *mode;       /* host array of nkeys, or NULL: the pa_dtype_t that produced each key */
+    uint32_t escalated;  /* out: number of keys recomputed in a wider mode */
+    uint32_t reserved;
+} pa_batch_info_t;
+
+/*
+ * pa_plan -- choose the transform for keys of n bits hashed to m bits.
+ * Paper Section 2.2 (FFT length n+r-1 for the standard Toeplitz matrix) and
+ * Algorithm 1 (a long FFT split into passes of short FFTs): the plan picks a
+ * power-of-two complex length L >= n+m-1, factors it into two or three
+ * passes, builds twiddle tables, and allocates the seed-spectrum slot (L
+ * complex values) on the current CUDA device. Work buffers are allocated by the
+ * first pa_hash_batch that needs them and kept until pa_plan_destroy.
+ *   n      key length in bits, 1 <= n <= 2^27
+ *   m      final-key length in bits, 1 <= m <= n
+ *   dtype  arithmetic of the transform (see pa_dtype_t)
+ *   out    receives the plan; owned by the caller, released with pa_plan_destroy
+ * Returns PA_EINVAL for bad sizes, PA_ENOMEM, PA_EUNSUPPORTED, PA_ECUDA.
+ */
+int pa_plan(uint64_t n, uint64_t m, pa_dtype_t dtype, pa_plan_t **out);
+
+/* Release a plan and all device memory it owns. NULL is accepted. Synchronizes the device. */
+int pa_plan_destroy(pa_plan_t *plan);
+
+/*
+ * pa_set_seed -- cache the spectrum of the Toeplitz seed (Eq. 4: FFT(V_n),
+ * computed once and reused by every key hashed with this seed).
+ *   seed_dev   device pointer, ceil(seed_bits/64) words, caller-owned, read during
+ *              the call only (stream-ordered)
+ *   seed_bits  must equal n+m-1 (PA_EINVAL otherwise)
+ *   stream     CUDA stream the transform is issued on; asynchronous
+ */
+int pa_set_seed(pa_plan_t *plan, const uint64_t *seed_dev, uint64_t seed_bits, pa_stream_t stream);
+
+/*
+ * pa_hash_batch -- y_k = T x_k mod 2 for nkeys keys that share the plan's seed
+ * (Eq. 3-4 for every key; two keys ride in one complex transform as its real
+ * and imaginary parts, the idea of Eq. 5-10 applied to two keys).
+ *   keys_dev          device pointer; key k starts at keys_dev + k*key_stride_words
+ *   nkeys             number of keys, >= 1
+ *   key_stride_words  >= ceil(n/64), even (16-byte alignment of every key)
+ *   out_dev           device pointer; final key k starts at out_dev + k*out_stride_words
+ *   out_stride_words  >= ceil(m/64), even
+ *   stream            CUDA stream; kernels are issued asynchronously on it
+ *   info              optional per-key diagnostics (may be NULL)
+ * Synchronization: in PA_FP32_GUARD mode, and in any mode when info != NULL, the
+ * call waits for the stream to read the rounding margins back (the guard of
+ * Section 5's precision question needs them on the host); otherwise it returns
+ * after issuing the kernels. Returns PA_ENOSEED if no seed was set.
+ */
+int pa_hash_batch(pa_plan_t *plan, const uint64_t *keys_dev, uint32_t nkeys, uint64_t key_stride_words,
+                  uint64_t *out_dev, uint64_t out_stride_words, pa_stream_t stream, pa_batch_info_t *info);
+
+/*
+ * pa_plan_set_guard -- rounding-margin threshold of the FP32 guard (default 0.25,
+ * the value the guard is specified with). A key whose margin max_i |w_i - rint(w_i)|
+ * exceeds it is recomputed in FP64. Lowering it (e.g. to -1) forces every key
+ * through the escalation path; tests use that to exercise it.
+ */
+int pa_plan_set_guard(pa_plan_t *plan, float threshold);
+
+/* Plan introspection (no GPU work): transform length L and pass lengths L1, L2, L3 (L3 = 1 for two passes). */
+int pa_plan_shape(const pa_plan_t *plan, uint64_t *L, uint32_t *L1, uint32_t *L2, uint32_t *L3);
+
+/*
+ * Kernel timing (measurement support, no counterpart in the paper). When enabled,
+ * every kernel launch of the plan is bracketed by CUDA events recorded on the
+ * launching stream. pa_profile_read waits for the recorded events, adds their
+ * elapsed times to per-kernel totals and returns them; reset != 0 clears the totals.
+ */
+typedef struct {
+    const char *name;      /* kernel family: "prep", "fwd_keys", "fwd_seed", "mid_fwd", "middle_conv", ... */
+    uint64_t launches;     /* launches since the last reset */
+    double total_ms;       /* summed event time */
+} pa_kernel_stat_t;
+
+#define PA_NUM_KERNEL_KINDS 8
+
+int pa_profile_enable(pa_plan_t *plan, int enable);
+/* stats: caller array of PA_NUM_KERNEL_KINDS entries; *count receives the number filled. */
+int pa_profile_read(pa_plan_t *plan, pa_kernel_stat_t *stats, int *count, int reset);
+
+/* Text for an error code; never NULL. */
+const char *pa_strerror(int code);
+
+/* The last CUDA runtime error string seen by this thread ("" if none). */
+const char *pa_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PA_H_ */

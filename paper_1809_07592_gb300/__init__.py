@@ -1,0 +1,214 @@
+"""GB300 FFT Toeplitz-hash privacy amplification: Python binding of libpa.so.
+
+Thin ctypes marshalling over the C ABI in ``include/pa.h``. Every step of the
+hash (bit unpacking, the FFT passes, the product with the seed spectrum,
+rounding, parity and packing) runs in libpa.so's CUDA kernels; PyTorch only
+provides device memory and streams. There is no CPU fallback: if libpa.so is
+not built, or no CUDA device is present, these calls raise.
+
+Names follow the C ABI: ``pa_plan``, ``pa_set_seed``, ``pa_hash_batch``, ...
+A key tensor holds packed bits (bit j in 64-bit word j // 64 at position
+j % 64); tensors are int64 on the device and reinterpreted as uint64.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+PA_OK = 0
+PA_EINVAL = -1
+PA_ENOMEM = -2
+PA_EAGAIN = -3
+PA_EPENDING = -4
+PA_ETIMEOUT = -5
+PA_EPRECISION = -6
+PA_ECUDA = -7
+PA_ENOSEED = -8
+PA_EUNSUPPORTED = -9
+
+PA_FP64 = 0
+PA_FP32_GUARD = 1
+PA_NTT64 = 2
+DTYPES = {"fp64": PA_FP64, "fp32_guard": PA_FP32_GUARD, "fp32": PA_FP32_GUARD, "ntt64": PA_NTT64}
+
+_lib = None
+
+
+class PAError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = f"{where}: {pa_strerror(code)}"
+        if code == PA_ECUDA:
+            msg += f" ({lib().pa_last_cuda_error().decode()})"
+        super().__init__(msg)
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("margin", ctypes.POINTER(ctypes.c_float)), ("mode", ctypes.POINTER(ctypes.c_int32)),
+                ("escalated", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
+
+
+PA_NUM_KERNEL_KINDS = 8
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libpa.so (built in-tree by ``build.build()``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libpa.so is not built at {path}; run __graft_entry__.build() first")
+    L = ctypes.CDLL(path)
+    vp, u64, u32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32
+    L.pa_plan.argtypes = [u64, u64, ctypes.c_int, ctypes.POINTER(vp)]
+    L.pa_plan_destroy.argtypes = [vp]
+    L.pa_set_seed.argtypes = [vp, vp, u64, vp]
+    L.pa_hash_batch.argtypes = [vp, vp, u32, u64, vp, u64, vp, ctypes.POINTER(BatchInfo)]
+    L.pa_plan_set_guard.argtypes = [vp, ctypes.c_float]
+    L.pa_plan_shape.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u32), ctypes.POINTER(u32),
+                                ctypes.POINTER(u32)]
+    L.pa_profile_enable.argtypes = [vp, ctypes.c_int]
+    L.pa_profile_read.argtypes = [vp, ctypes.POINTER(KernelStat), ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+    L.pa_strerror.argtypes = [ctypes.c_int]
+    L.pa_strerror.restype = ctypes.c_char_p
+    L.pa_last_cuda_error.argtypes = []
+    L.pa_last_cuda_error.restype = ctypes.c_char_p
+    for name in ("pa_plan", "pa_plan_destroy", "pa_set_seed", "pa_hash_batch", "pa_plan_set_guard",
+                 "pa_plan_shape", "pa_profile_enable", "pa_profile_read"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != PA_OK:
+        raise PAError(rc, where)
+
+
+def pa_strerror(code: int) -> str:
+    return lib().pa_strerror(code).decode()
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(t) -> int:
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    return t.data_ptr()
+
+
+def pa_plan(n: int, m: int, dtype=PA_FP32_GUARD) -> int:
+    if isinstance(dtype, str):
+        dtype = DTYPES[dtype]
+    h = ctypes.c_void_p()
+    _check(lib().pa_plan(n, m, dtype, ctypes.byref(h)), "pa_plan")
+    return h.value
+
+
+def pa_plan_destroy(plan: int) -> None:
+    _check(lib().pa_plan_destroy(plan), "pa_plan_destroy")
+
+
+def pa_plan_set_guard(plan: int, threshold: float) -> None:
+    _check(lib().pa_plan_set_guard(plan, threshold), "pa_plan_set_guard")
+
+
+def pa_plan_shape(plan: int):
+    L = ctypes.c_uint64()
+    a, b, c = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+    _check(lib().pa_plan_shape(plan, ctypes.byref(L), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "pa_plan_shape")
+    return L.value, a.value, b.value, c.value
+
+
+def pa_set_seed(plan: int, seed, seed_bits: int, stream=None) -> None:
+    _check(lib().pa_set_seed(plan, _ptr(seed), seed_bits, _stream_handle(stream)), "pa_set_seed")
+
+
+def pa_hash_batch(plan: int, keys, nkeys: int, key_stride_words: int, out, out_stride_words: int, stream=None,
+                  info: bool = False):
+    """Returns None, or (margins list, modes list, escalated) when ``info`` is set."""
+    if info:
+        marg = (ctypes.c_float * nkeys)()
+        mode = (ctypes.c_int32 * nkeys)()
+        bi = BatchInfo(ctypes.cast(marg, ctypes.POINTER(ctypes.c_float)),
+                       ctypes.cast(mode, ctypes.POINTER(ctypes.c_int32)), 0, 0)
+        _check(lib().pa_hash_batch(plan, _ptr(keys), nkeys, key_stride_words, _ptr(out), out_stride_words,
+                                   _stream_handle(stream), ctypes.byref(bi)), "pa_hash_batch")
+        return list(marg), list(mode), bi.escalated
+    _check(lib().pa_hash_batch(plan, _ptr(keys), nkeys, key_stride_words, _ptr(out), out_stride_words,
+                               _stream_handle(stream), None), "pa_hash_batch")
+    return None
+
+
+def pa_profile_enable(plan: int, enable: bool = True) -> None:
+    _check(lib().pa_profile_enable(plan, 1 if enable else 0), "pa_profile_enable")
+
+
+def pa_profile_read(plan: int, reset: bool = False) -> dict:
+    """{kernel family: (launches, total_ms)} accumulated since the last reset."""
+    arr = (KernelStat * PA_NUM_KERNEL_KINDS)()
+    cnt = ctypes.c_int()
+    _check(lib().pa_profile_read(plan, arr, ctypes.byref(cnt), 1 if reset else 0), "pa_profile_read")
+    return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms) for i in range(cnt.value)}
+
+
+class Plan:
+    """Owns one pa_plan handle; a convenience wrapper over the functions above."""
+
+    def __init__(self, n: int, m: int, dtype=PA_FP32_GUARD):
+        self.n, self.m = n, m
+        self.handle = pa_plan(n, m, dtype)
+
+    def words_in(self) -> int:
+        return (self.n + 63) // 64
+
+    def words_out(self) -> int:
+        return (self.m + 63) // 64
+
+    def set_seed(self, seed, stream=None):
+        pa_set_seed(self.handle, seed, self.n + self.m - 1, stream)
+
+    def hash(self, keys, out=None, stream=None, info=False):
+        """keys: (nkeys, stride) int64 CUDA tensor (stride even or nkeys == 1)."""
+        import torch
+        if keys.dim() == 1:
+            keys = keys.view(1, -1)
+        nkeys, kstride = keys.shape
+        if out is None:
+            ostride = self.words_out() + (self.words_out() & 1)
+            out = torch.empty((nkeys, ostride), dtype=torch.int64, device=keys.device)
+        r = pa_hash_batch(self.handle, keys, nkeys, kstride, out, out.shape[1], stream, info)
+        return (out, r) if info else out
+
+    def shape(self):
+        return pa_plan_shape(self.handle)
+
+    def close(self):
+        if self.handle:
+            pa_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,508 @@
+// pa_api.cu -- the C ABI declared in include/pa.h: plans, seed spectra, batched hashing.
+//
+// A plan fixes (n, m, dtype) and the transform: complex length L, a power of
+// two >= n+m-1 (paper Section 2.2: the FFT length of the standard Toeplitz
+// hash is n+r-1), split into two or three passes (paper Algorithm 1 splits a
+// long FFT into short row and column FFTs with a twiddle step in between).
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "pa.h"
+#include "pa_launch.h"
+
+using namespace pa;
+
+namespace {
+
+thread_local std::string g_last_cuda_error;
+
+int cuda_fail(cudaError_t e, const char *what) {
+    g_last_cuda_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return PA_ECUDA;
+}
+
+#define PA_CUDA(call)                                   \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Pass lengths (log2) for a complex transform of length 2^lgL. Two levels
+// while the innermost (contiguous) transform fits one CTA's shared memory,
+// three levels beyond.
+struct Shape3 {
+    int lg1, lg2, lg3;  // lg3 == 0: two levels, lg2 is the innermost
+};
+
+Shape3 choose_shape(int lgL, bool fp64) {
+    const int maxMid = fp64 ? MaxLgMiddle<double>::v : MaxLgMiddle<float>::v;
+    Shape3 s{0, 0, 0};
+    int lg1 = lgL - 12;
+    if (lg1 < kMinLgStrided) lg1 = kMinLgStrided;
+    if (lg1 > kMaxLgStrided) lg1 = kMaxLgStrided;
+    if (lgL - lg1 <= maxMid) {
+        s.lg1 = lg1;
+        s.lg2 = lgL - lg1;
+        return s;
+    }
+    // three levels: a short middle strided pass of 2^6, the rest split
+    const int lgm = kMinLgStrided;
+    int l1 = lgL - 12 - lgm;
+    if (l1 > kMaxLgStrided) l1 = kMaxLgStrided;
+    if (l1 < kMinLgStrided) l1 = kMinLgStrided;
+    s.lg1 = l1;
+    s.lg2 = lgm;
+    s.lg3 = lgL - l1 - lgm;
+    return s;
+}
+
+}  // namespace
+
+struct pa_plan {
+    uint64_t n = 0, m = 0;
+    pa_dtype_t dtype = PA_FP64;
+    int device = 0;
+    int lgL = 0;
+    uint64_t L = 0;
+    Shape3 shape{};
+    uint32_t twB = 0;
+    void *tw_hi = nullptr, *tw_lo = nullptr;
+    void *spec = nullptr;        // L complex values, seed spectrum in digit-reversed order, times 1/L
+    void *work = nullptr;        // work_pairs * L complex values
+    uint32_t work_pairs = 0;
+    uint32_t max_chunk_pairs = 1;
+    uint32_t *popc = nullptr;    // per key
+    uint32_t *marg = nullptr;    // per key, float bits
+    uint32_t key_cap = 0;
+    float *h_marg = nullptr;     // pinned
+    uint32_t h_cap = 0;
+    uint64_t *seed_copy = nullptr;  // the seed bits, kept for an escalation plan
+    bool seeded = false;
+    float guard = 0.25f;
+    pa_plan_t *fallback = nullptr;    // FP64 plan used to recompute keys that fail the FP32 guard
+    std::mutex mu;
+    // kernel timing
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_a, ev_b;  // event pairs, reused
+    std::vector<int> ev_kind;             // kind of each recorded pair (pending)
+    size_t ev_used = 0;
+    uint64_t launches[PA_NUM_KERNEL_KINDS] = {};
+    double total_ms[PA_NUM_KERNEL_KINDS] = {};
+};
+
+namespace {
+
+enum Kind { K_PREP = 0, K_FWD_KEYS, K_FWD_SEED, K_MID_FWD, K_MIDDLE_CONV, K_MIDDLE_SPEC, K_MID_INV, K_INV_BITS };
+const char *kKindNames[PA_NUM_KERNEL_KINDS] = {"prep",        "fwd_keys",    "fwd_seed", "mid_fwd",
+                                               "middle_conv", "middle_spec", "mid_inv",  "inv_bits"};
+
+// Brackets one launch with a pair of events when timing is on.
+struct Timed {
+    pa_plan_t *p;
+    int kind;
+    cudaStream_t st;
+    size_t slot = (size_t)-1;
+    Timed(pa_plan_t *p_, int kind_, cudaStream_t st_) : p(p_), kind(kind_), st(st_) {
+        if (!p->prof) return;
+        if (p->ev_used == p->ev_a.size()) {
+            cudaEvent_t a, b;
+            if (cudaEventCreate(&a) != cudaSuccess) return;
+            if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return; }
+            p->ev_a.push_back(a);
+            p->ev_b.push_back(b);
+            p->ev_kind.push_back(0);
+        }
+        slot = p->ev_used++;
+        p->ev_kind[slot] = kind;
+        cudaEventRecord(p->ev_a[slot], st);
+    }
+    ~Timed() {
+        if (slot != (size_t)-1) cudaEventRecord(p->ev_b[slot], st);
+    }
+};
+
+void collect_events(pa_plan_t *p) {
+    for (size_t i = 0; i < p->ev_used; ++i) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(p->ev_b[i]) == cudaSuccess && cudaEventElapsedTime(&ms, p->ev_a[i], p->ev_b[i]) == cudaSuccess) {
+            p->total_ms[p->ev_kind[i]] += ms;
+            p->launches[p->ev_kind[i]] += 1;
+        }
+    }
+    p->ev_used = 0;
+}
+
+size_t elem_bytes(pa_dtype_t d) { return d == PA_FP32_GUARD ? sizeof(float2) : sizeof(double2); }
+
+template <typename T>
+int build_twiddles(pa_plan_t *p) {
+    const int lgL = p->lgL;
+    const uint32_t B = (uint32_t)(lgL + 1) / 2;
+    const uint64_t nhi = 1ull << (lgL - B), nlo = 1ull << B;
+    std::vector<cx<T>> hi(nhi), lo(nlo);
+    const double L = (double)p->L;
+    const double two_pi = 6.283185307179586476925286766559;
+    for (uint64_t h = 0; h < nhi; ++h) {
+        const double a = two_pi * (double)(h << B) / L;
+        hi[h].x = (T)std::cos(a);
+        hi[h].y = (T)-std::sin(a);
+    }
+    for (uint64_t l = 0; l < nlo; ++l) {
+        const double a = two_pi * (double)l / L;
+        lo[l].x = (T)std::cos(a);
+        lo[l].y = (T)-std::sin(a);
+    }
+    PA_CUDA(cudaMalloc(&p->tw_hi, nhi * sizeof(cx<T>)));
+    PA_CUDA(cudaMalloc(&p->tw_lo, nlo * sizeof(cx<T>)));
+    PA_CUDA(cudaMemcpy(p->tw_hi, hi.data(), nhi * sizeof(cx<T>), cudaMemcpyHostToDevice));
+    PA_CUDA(cudaMemcpy(p->tw_lo, lo.data(), nlo * sizeof(cx<T>), cudaMemcpyHostToDevice));
+    p->twB = B;
+    return PA_OK;
+}
+
+template <typename T>
+TwTab<T> tw_of(const pa_plan_t *p) {
+    TwTab<T> t;
+    t.hi = static_cast<const cx<T> *>(p->tw_hi);
+    t.lo = static_cast<const cx<T> *>(p->tw_lo);
+    t.B = p->twB;
+    t.lgL = (uint32_t)p->lgL;
+    return t;
+}
+
+int ensure_work(pa_plan_t *p, uint32_t pairs) {
+    if (pairs <= p->work_pairs) return PA_OK;
+    if (p->work) {
+        cudaError_t e = cudaFree(p->work);
+        p->work = nullptr;
+        p->work_pairs = 0;
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFree(work)");
+    }
+    cudaError_t e = cudaMalloc(&p->work, (size_t)pairs * p->L * elem_bytes(p->dtype));
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return PA_ENOMEM;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(work)");
+    p->work_pairs = pairs;
+    return PA_OK;
+}
+
+int ensure_keys(pa_plan_t *p, uint32_t nkeys) {
+    if (nkeys <= p->key_cap) return PA_OK;
+    if (p->popc) cudaFree(p->popc);
+    if (p->marg) cudaFree(p->marg);
+    p->popc = p->marg = nullptr;
+    p->key_cap = 0;
+    PA_CUDA(cudaMalloc(&p->popc, (size_t)nkeys * sizeof(uint32_t)));
+    PA_CUDA(cudaMalloc(&p->marg, (size_t)nkeys * sizeof(uint32_t)));
+    p->key_cap = nkeys;
+    return PA_OK;
+}
+
+int ensure_host(pa_plan_t *p, uint32_t nkeys) {
+    if (nkeys <= p->h_cap) return PA_OK;
+    if (p->h_marg) cudaFreeHost(p->h_marg);
+    p->h_marg = nullptr;
+    p->h_cap = 0;
+    PA_CUDA(cudaMallocHost(&p->h_marg, (size_t)nkeys * sizeof(float)));
+    p->h_cap = nkeys;
+    return PA_OK;
+}
+
+// Pairs per launch chunk: bounded by the work-buffer budget and by the grid's
+// y extent (65535) of the three-level middle strided pass.
+uint32_t chunk_pairs_limit(const pa_plan_t *p) {
+    size_t budget = (size_t)4 << 30;  // 4 GiB of work buffer
+    if (const char *s = std::getenv("PA_WORK_BYTES")) budget = (size_t)std::strtoull(s, nullptr, 10);
+    size_t per = (size_t)p->L * elem_bytes(p->dtype);
+    size_t lim = budget / per;
+    if (lim < 1) lim = 1;
+    if (p->shape.lg3) {
+        size_t nblk = p->L >> (p->shape.lg2 + p->shape.lg3);
+        size_t y = 65535 / nblk;
+        if (y < lim) lim = y;
+    }
+    if (lim > 65535) lim = 65535;
+    return (uint32_t)lim;
+}
+
+template <typename T>
+int run_seed(pa_plan_t *p, const uint64_t *seed, cudaStream_t st) {
+    const TwTab<T> tw = tw_of<T>(p);
+    cx<T> *W = static_cast<cx<T> *>(p->work);
+    cx<T> *spec = static_cast<cx<T> *>(p->spec);
+    const Shape3 &s = p->shape;
+    { Timed t_(p, K_FWD_SEED, st); PA_CUDA(launch_fwd_seed<T>(s.lg1, seed, p->n, p->m, W, p->L, tw, st)); }
+    int inner = s.lg2;
+    if (s.lg3) {
+        { Timed t_(p, K_MID_FWD, st); PA_CUDA(launch_mid<T>(s.lg2, false, W, p->L, (uint32_t)s.lg3, 1, tw, st)); }
+        inner = s.lg3;
+    }
+    { Timed t_(p, K_MIDDLE_SPEC, st); PA_CUDA(launch_middle<T>(inner, 1, W, spec, p->L, 1, tw, (T)(1.0 / (double)p->L), st)); }
+    return PA_OK;
+}
+
+template <typename T>
+int run_keys(pa_plan_t *p, const uint64_t *keys, uint32_t nkeys, uint64_t kstride, uint64_t *out,
+             uint64_t ostride, uint32_t *popc, uint32_t *marg, cudaStream_t st) {
+    const TwTab<T> tw = tw_of<T>(p);
+    cx<T> *W = static_cast<cx<T> *>(p->work);
+    cx<T> *spec = static_cast<cx<T> *>(p->spec);
+    const Shape3 &s = p->shape;
+    { Timed t_(p, K_PREP, st); PA_CUDA(launch_prep(keys, nkeys, kstride, p->n, popc, marg, st)); }
+    const uint32_t npairs = (nkeys + 1) / 2;
+    for (uint32_t p0 = 0; p0 < npairs; p0 += p->work_pairs) {
+        const uint32_t pairs = (npairs - p0 < p->work_pairs) ? npairs - p0 : p->work_pairs;
+        const uint32_t k0 = 2 * p0;
+        const uint32_t nk = (nkeys - k0 < 2 * pairs) ? nkeys - k0 : 2 * pairs;
+        const uint64_t *kp = keys + (uint64_t)k0 * kstride;
+        uint64_t *op = out + (uint64_t)k0 * ostride;
+        { Timed t_(p, K_FWD_KEYS, st); PA_CUDA(launch_fwd_keys<T>(s.lg1, kp, nk, kstride, p->n, W, p->L, pairs, tw, st)); }
+        if (s.lg3) {
+            { Timed t_(p, K_MID_FWD, st); PA_CUDA(launch_mid<T>(s.lg2, false, W, p->L, (uint32_t)s.lg3, pairs, tw, st)); }
+            { Timed t_(p, K_MIDDLE_CONV, st); PA_CUDA(launch_middle<T>(s.lg3, 0, W, spec, p->L, pairs, tw, (T)1, st)); }
+            { Timed t_(p, K_MID_INV, st); PA_CUDA(launch_mid<T>(s.lg2, true, W, p->L, (uint32_t)s.lg3, pairs, tw, st)); }
+        } else {
+            { Timed t_(p, K_MIDDLE_CONV, st); PA_CUDA(launch_middle<T>(s.lg2, 0, W, spec, p->L, pairs, tw, (T)1, st)); }
+        }
+        { Timed t_(p, K_INV_BITS, st); PA_CUDA(launch_inv_bits<T>(s.lg1, W, p->L, p->m, nk, popc + k0, marg + k0, op, ostride, pairs, tw, st)); }
+    }
+    return PA_OK;
+}
+
+void free_plan(pa_plan_t *p) {
+    if (!p) return;
+    if (p->fallback) free_plan(p->fallback);
+    cudaFree(p->tw_hi);
+    cudaFree(p->tw_lo);
+    cudaFree(p->spec);
+    cudaFree(p->work);
+    cudaFree(p->popc);
+    cudaFree(p->marg);
+    cudaFree(p->seed_copy);
+    if (p->h_marg) cudaFreeHost(p->h_marg);
+    for (cudaEvent_t e : p->ev_a) cudaEventDestroy(e);
+    for (cudaEvent_t e : p->ev_b) cudaEventDestroy(e);
+    delete p;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pa_strerror(int code) {
+    switch (code) {
+        case PA_OK: return "PA_OK: success";
+        case PA_EINVAL: return "PA_EINVAL: invalid argument (size, pointer, alignment, stride or handle)";
+        case PA_ENOMEM: return "PA_ENOMEM: device or pinned host memory exhausted";
+        case PA_EAGAIN: return "PA_EAGAIN: admission cap reached and queue full";
+        case PA_EPENDING: return "PA_EPENDING: request not complete yet";
+        case PA_ETIMEOUT: return "PA_ETIMEOUT: bounded wait expired";
+        case PA_EPRECISION: return "PA_EPRECISION: no precision mode rounded unambiguously";
+        case PA_ECUDA: return "PA_ECUDA: CUDA runtime error";
+        case PA_ENOSEED: return "PA_ENOSEED: pa_set_seed has not been called on this plan";
+        case PA_EUNSUPPORTED: return "PA_EUNSUPPORTED: size or mode not supported by this build";
+        default: return "unknown pa error code";
+    }
+}
+
+const char *pa_last_cuda_error(void) { return g_last_cuda_error.c_str(); }
+
+int pa_plan(uint64_t n, uint64_t m, pa_dtype_t dtype, pa_plan_t **out) {
+    if (!out) return PA_EINVAL;
+    *out = nullptr;
+    if (n == 0 || m == 0 || m > n || n > (1ull << 27)) return PA_EINVAL;
+    if (dtype != PA_FP64 && dtype != PA_FP32_GUARD && dtype != PA_NTT64) return PA_EINVAL;
+    if (dtype == PA_NTT64) return PA_EUNSUPPORTED;
+    pa_plan_t *p = new pa_plan_t();
+    p->n = n;
+    p->m = m;
+    p->dtype = dtype;
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        delete p;
+        return cuda_fail(cudaGetLastError(), "cudaGetDevice");
+    }
+    const uint64_t need = n + m - 1;
+    int lgL = 12;
+    while ((1ull << lgL) < need) ++lgL;
+    if (lgL > 28) {
+        delete p;
+        return PA_EUNSUPPORTED;
+    }
+    p->lgL = lgL;
+    p->L = 1ull << lgL;
+    p->shape = choose_shape(lgL, dtype == PA_FP64);
+    int rc = (dtype == PA_FP32_GUARD) ? build_twiddles<float>(p) : build_twiddles<double>(p);
+    if (rc != PA_OK) {
+        free_plan(p);
+        return rc;
+    }
+    cudaError_t e = cudaMalloc(&p->spec, (size_t)p->L * elem_bytes(dtype));
+    if (e != cudaSuccess) {
+        free_plan(p);
+        if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();
+            return PA_ENOMEM;
+        }
+        return cuda_fail(e, "cudaMalloc(spec)");
+    }
+    p->max_chunk_pairs = chunk_pairs_limit(p);
+    *out = p;
+    return PA_OK;
+}
+
+int pa_plan_destroy(pa_plan_t *plan) {
+    if (!plan) return PA_OK;
+    DeviceGuard g(plan->device);
+    cudaDeviceSynchronize();
+    free_plan(plan);
+    return PA_OK;
+}
+
+int pa_plan_shape(const pa_plan_t *p, uint64_t *L, uint32_t *L1, uint32_t *L2, uint32_t *L3) {
+    if (!p) return PA_EINVAL;
+    if (L) *L = p->L;
+    if (L1) *L1 = 1u << p->shape.lg1;
+    if (L2) *L2 = 1u << p->shape.lg2;
+    if (L3) *L3 = p->shape.lg3 ? (1u << p->shape.lg3) : 1u;
+    return PA_OK;
+}
+
+int pa_plan_set_guard(pa_plan_t *p, float threshold) {
+    if (!p) return PA_EINVAL;
+    p->guard = threshold;
+    return PA_OK;
+}
+
+int pa_profile_enable(pa_plan_t *p, int enable) {
+    if (!p) return PA_EINVAL;
+    std::lock_guard<std::mutex> lk(p->mu);
+    p->prof = enable != 0;
+    return PA_OK;
+}
+
+int pa_profile_read(pa_plan_t *p, pa_kernel_stat_t *stats, int *count, int reset) {
+    if (!p || !stats || !count) return PA_EINVAL;
+    std::lock_guard<std::mutex> lk(p->mu);
+    DeviceGuard g(p->device);
+    collect_events(p);
+    int c = 0;
+    for (int k = 0; k < PA_NUM_KERNEL_KINDS; ++k) {
+        stats[c].name = kKindNames[k];
+        stats[c].launches = p->launches[k];
+        stats[c].total_ms = p->total_ms[k];
+        ++c;
+        if (reset) {
+            p->launches[k] = 0;
+            p->total_ms[k] = 0.0;
+        }
+    }
+    *count = c;
+    return PA_OK;
+}
+
+int pa_set_seed(pa_plan_t *p, const uint64_t *seed_dev, uint64_t seed_bits, pa_stream_t stream) {
+    if (!p || !seed_dev || !aligned16(seed_dev)) return PA_EINVAL;
+    if (seed_bits != p->n + p->m - 1) return PA_EINVAL;
+    std::lock_guard<std::mutex> lk(p->mu);
+    DeviceGuard g(p->device);
+    if (!g.ok) return cuda_fail(cudaGetLastError(), "cudaSetDevice");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int rc = ensure_work(p, 1);
+    if (rc != PA_OK) return rc;
+    const size_t sw = (size_t)((seed_bits + 63) / 64);
+    if (!p->seed_copy) PA_CUDA(cudaMalloc(&p->seed_copy, sw * sizeof(uint64_t)));
+    PA_CUDA(cudaMemcpyAsync(p->seed_copy, seed_dev, sw * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
+    rc = (p->dtype == PA_FP32_GUARD) ? run_seed<float>(p, p->seed_copy, st) : run_seed<double>(p, p->seed_copy, st);
+    if (rc != PA_OK) return rc;
+    p->seeded = true;
+    if (p->fallback) p->fallback->seeded = false;  // re-seeded lazily on the next escalation
+    return PA_OK;
+}
+
+int pa_hash_batch(pa_plan_t *p, const uint64_t *keys_dev, uint32_t nkeys, uint64_t key_stride_words,
+                  uint64_t *out_dev, uint64_t out_stride_words, pa_stream_t stream, pa_batch_info_t *info) {
+    if (!p || !keys_dev || !out_dev || nkeys == 0) return PA_EINVAL;
+    if (!aligned16(keys_dev) || !aligned16(out_dev)) return PA_EINVAL;
+    if (key_stride_words < (p->n + 63) / 64 || out_stride_words < (p->m + 63) / 64) return PA_EINVAL;
+    if ((nkeys > 1 && (key_stride_words & 1)) || (nkeys > 1 && (out_stride_words & 1))) return PA_EINVAL;
+    if (!p->seeded) return PA_ENOSEED;
+    std::lock_guard<std::mutex> lk(p->mu);
+    DeviceGuard g(p->device);
+    if (!g.ok) return cuda_fail(cudaGetLastError(), "cudaSetDevice");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const uint32_t npairs = (nkeys + 1) / 2;
+    uint32_t want = npairs < p->max_chunk_pairs ? npairs : p->max_chunk_pairs;
+    int rc = ensure_work(p, want);
+    if (rc != PA_OK) return rc;
+    rc = ensure_keys(p, nkeys);
+    if (rc != PA_OK) return rc;
+    rc = (p->dtype == PA_FP32_GUARD)
+             ? run_keys<float>(p, keys_dev, nkeys, key_stride_words, out_dev, out_stride_words, p->popc, p->marg, st)
+             : run_keys<double>(p, keys_dev, nkeys, key_stride_words, out_dev, out_stride_words, p->popc, p->marg,
+                                st);
+    if (rc != PA_OK) return rc;
+    if (info) info->escalated = 0;
+    const bool need_margins = (p->dtype == PA_FP32_GUARD) || info != nullptr;
+    if (!need_margins) return PA_OK;
+
+    rc = ensure_host(p, nkeys);
+    if (rc != PA_OK) return rc;
+    PA_CUDA(cudaMemcpyAsync(p->h_marg, p->marg, (size_t)nkeys * sizeof(float), cudaMemcpyDeviceToHost, st));
+    PA_CUDA(cudaStreamSynchronize(st));
+    uint32_t escalated = 0;
+    for (uint32_t k = 0; k < nkeys; ++k) {
+        float mk_ = p->h_marg[k];
+        int32_t mode = (int32_t)p->dtype;
+        if (!(mk_ <= p->guard)) {
+            if (p->dtype != PA_FP32_GUARD) return PA_EPRECISION;
+            // Recompute this key in FP64 (the guard's escalation).
+            if (!p->fallback) {
+                pa_plan_t *fb = nullptr;
+                rc = pa_plan(p->n, p->m, PA_FP64, &fb);
+                if (rc != PA_OK) return rc;
+                p->fallback = fb;
+            }
+            if (!p->fallback->seeded) {
+                rc = pa_set_seed(p->fallback, p->seed_copy, p->n + p->m - 1, stream);
+                if (rc != PA_OK) return rc;
+            }
+            float m2 = 0.f;
+            int32_t mode2 = 0;
+            pa_batch_info_t sub{&m2, &mode2, 0, 0};
+            rc = pa_hash_batch(p->fallback, keys_dev + (uint64_t)k * key_stride_words, 1, key_stride_words,
+                               out_dev + (uint64_t)k * out_stride_words, out_stride_words, stream, &sub);
+            if (rc != PA_OK) return rc;
+            mk_ = m2;
+            mode = mode2;
+            ++escalated;
+        }
+        if (info && info->margin) info->margin[k] = mk_;
+        if (info && info->mode) info->mode[k] = mode;
+    }
+    if (info) info->escalated = escalated;
+    return PA_OK;
+}
+
+}  // extern "C"

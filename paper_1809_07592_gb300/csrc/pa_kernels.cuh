@@ -1,0 +1,238 @@
+// pa_kernels.cuh -- the pass kernels of the FFT Toeplitz hash.
+//
+// Index conventions for a transform of complex length L = L1 * L2 (two
+// levels) or L1 * L2 * L3 (three levels). Element t of a length-L vector lives
+// at offset t of its work slot; a pass at level j with transform length LEN and
+// stride S treats the slot as blocks of LEN*S elements, each holding S
+// interleaved columns of LEN elements (element a of column u at a*S + u).
+//
+//   forward level j (decimation in frequency, paper Algorithm 1's "row FFT
+//   then twiddle W[i*j]"): X[k] = sum_a x[a] w_LEN^{a k}, then
+//   X[k] *= w_{LEN*S}^{k u}, stored back at k*S + u.
+//   inverse level j: x[k] *= w_{LEN*S}^{-k u}, then the unscaled inverse DFT.
+//
+// The innermost level (S = 1, contiguous) fuses the last forward step, the
+// pointwise product with the cached seed spectrum (Eq. 4's FFT(V) . FFT(X))
+// and the first inverse step. The seed spectrum already carries the 1/L of
+// the inverse transform.
+//
+// Encoding (the value that is rounded): key bits x_j in {0,1}; seed bits
+// enter as sigma = 1 - 2 s in {+1,-1} and are rotated so the wanted window of
+// the linear convolution lands at positions 0..m-1:
+//     r_i = sum_j sigma[i - j + n - 1] x_j = P - 2 c_i,
+// where c_i = sum_j s[i-j+n-1] x_j is the GF(2) row count and P = popcount(x).
+// So y_i = c_i mod 2 = rint((P - r_i)/2) mod 2, and since 4 | (P - P mod 4)
+// only P mod 4 enters: y_i = rint(w_i) mod 2 with w_i = ((P mod 4) - r_i)/2.
+// |r_i| grows like sqrt(n) instead of n, which keeps FP32 rounding far from
+// the 0.5 cliff (the precision concern of the paper's Section 5).
+#pragma once
+
+#include "fft_core.cuh"
+
+namespace pa {
+
+// ---------------------------------------------------------------------------
+// popcount P of each key (bits < n) and reset of its rounding margin.
+__global__ void k_prep(const uint64_t *__restrict__ keys, uint32_t nkeys, uint64_t kstride, uint64_t n,
+                       uint32_t *__restrict__ popc, uint32_t *__restrict__ margin_bits);
+
+// ---------------------------------------------------------------------------
+// Level-1 forward pass from packed key bits. Grid (S/COLS, pairs); pair p
+// carries key 2p in the real part and key 2p+1 (if any) in the imaginary part.
+template <typename T, int LEN, int COLS, int E>
+__global__ void __launch_bounds__(COLS * LEN / E)
+    k_fwd_keys(const uint64_t *__restrict__ keys, uint32_t nkeys, uint64_t kstride, uint64_t n,
+               cx<T> *__restrict__ W, uint64_t L, TwTab<T> tw) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T> *sm = reinterpret_cast<cx<T> *>(smem_raw);
+    const uint32_t col = threadIdx.x % COLS, tq = threadIdx.x / COLS;
+    const uint64_t S = L >> ilog2(LEN);
+    const uint64_t u = (uint64_t)blockIdx.x * COLS + col;
+    const uint32_t pair = blockIdx.y;
+    const uint64_t *ka = keys + (uint64_t)(2 * pair) * kstride;
+    const bool has_b = 2 * pair + 1 < nkeys;
+    const uint64_t *kb = keys + (uint64_t)(2 * pair + (has_b ? 1 : 0)) * kstride;
+    cx<T> v[E];
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+        const uint64_t t = (uint64_t)idx_r0<LEN, E>(tq, s) * S + u;
+        T xa = 0, xb = 0;
+        if (t < n) {
+            xa = (T)((__ldg(ka + (t >> 6)) >> (t & 63)) & 1u);
+            if (has_b) xb = (T)((__ldg(kb + (t >> 6)) >> (t & 63)) & 1u);
+        }
+        v[s] = mk<T>(xa, xb);
+    }
+    cta_fft<T, LEN, COLS, E, false>(sm, v, tq, col, tw);
+    cx<T> *w = W + (uint64_t)pair * L;
+    // k = tq + s*TC: w_L^{k u} = w_L^{tq u} * (w_L^{TC u})^s
+    twiddle_chain<T, false, E>(v, tw, (uint32_t)(tq * u), (uint32_t)((LEN / E) * u));
+#pragma unroll
+    for (int s = 0; s < E; ++s) w[(uint64_t)idx_e<LEN, E>(tq, s) * S + u] = v[s];
+}
+
+// Level-1 forward pass of the rotated, +-1 encoded seed (real input).
+template <typename T, int LEN, int COLS, int E>
+__global__ void __launch_bounds__(COLS * LEN / E)
+    k_fwd_seed(const uint64_t *__restrict__ seed, uint64_t n, uint64_t m, cx<T> *__restrict__ W, uint64_t L,
+               TwTab<T> tw) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T> *sm = reinterpret_cast<cx<T> *>(smem_raw);
+    const uint32_t col = threadIdx.x % COLS, tq = threadIdx.x / COLS;
+    const uint64_t S = L >> ilog2(LEN);
+    const uint64_t u = (uint64_t)blockIdx.x * COLS + col;
+    const uint64_t sbits = n + m - 1;
+    cx<T> v[E];
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+        const uint64_t pos = (uint64_t)idx_r0<LEN, E>(tq, s) * S + u;
+        uint64_t j = pos + n - 1;  // seed index whose value sits at rotated position pos
+        if (j >= L) j -= L;
+        T val = 0;
+        if (j < sbits) val = ((__ldg(seed + (j >> 6)) >> (j & 63)) & 1u) ? (T)-1 : (T)1;
+        v[s] = mk<T>(val, (T)0);
+    }
+    cta_fft<T, LEN, COLS, E, false>(sm, v, tq, col, tw);
+    twiddle_chain<T, false, E>(v, tw, (uint32_t)(tq * u), (uint32_t)((LEN / E) * u));
+#pragma unroll
+    for (int s = 0; s < E; ++s) W[(uint64_t)idx_e<LEN, E>(tq, s) * S + u] = v[s];
+}
+
+// Middle-level strided pass (three-level plans only), forward or inverse.
+// Grid (S/COLS, blocks * pairs) with blocks = L / (LEN * S).
+template <typename T, int LEN, int COLS, int E, bool INV>
+__global__ void __launch_bounds__(COLS * LEN / E)
+    k_mid(cx<T> *__restrict__ W, uint64_t L, uint32_t lgS, TwTab<T> tw) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T> *sm = reinterpret_cast<cx<T> *>(smem_raw);
+    const uint32_t col = threadIdx.x % COLS, tq = threadIdx.x / COLS;
+    const uint64_t S = 1ull << lgS;
+    const uint32_t lgBlk = ilog2(LEN) + lgS;
+    const uint64_t nblk = L >> lgBlk;
+    const uint64_t pair = blockIdx.y / nblk, blk = blockIdx.y % nblk;
+    const uint32_t u = blockIdx.x * COLS + col;
+    const uint32_t sh = tw.lgL - lgBlk;  // w_{LEN*S}^{e} = w_L^{e << sh}
+    cx<T> *w = W + pair * L + (blk << lgBlk);
+    cx<T> v[E];
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+        const uint32_t a = INV ? idx_e<LEN, E>(tq, s) : idx_r0<LEN, E>(tq, s);
+        v[s] = w[(uint64_t)a * S + u];
+    }
+    if (INV) twiddle_chain<T, true, E>(v, tw, (tq * u) << sh, ((LEN / E) * u) << sh);
+    cta_fft<T, LEN, COLS, E, INV>(sm, v, tq, col, tw);
+    if (!INV) twiddle_chain<T, false, E>(v, tw, (tq * u) << sh, ((LEN / E) * u) << sh);
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+        const uint32_t a = INV ? idx_r0<LEN, E>(tq, s) : idx_e<LEN, E>(tq, s);
+        w[(uint64_t)a * S + u] = v[s];
+    }
+}
+
+// Innermost level: contiguous rows of LEN elements. MODE 0: forward, times
+// the seed spectrum, inverse (the fused convolution step). MODE 1: forward
+// only, scaled by 1/L, written as the seed spectrum.
+template <typename T, int LEN, int E, int MODE>
+__global__ void __launch_bounds__(LEN / E)
+    k_middle(cx<T> *__restrict__ W, cx<T> *__restrict__ spec, uint64_t L, TwTab<T> tw, T scale) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T> *sm = reinterpret_cast<cx<T> *>(smem_raw);
+    const uint32_t tq = threadIdx.x;
+    const uint64_t row = blockIdx.x, pair = blockIdx.y;
+    cx<T> *w = W + pair * L + row * LEN;
+    cx<T> *sp = spec + row * LEN;
+    cx<T> v[E];
+#pragma unroll
+    for (int s = 0; s < E; ++s) v[s] = w[idx_r0<LEN, E>(tq, s)];
+    cta_fft<T, LEN, 1, E, false>(sm, v, tq, 0, tw);
+    if (MODE == 1) {
+#pragma unroll
+        for (int s = 0; s < E; ++s) sp[idx_e<LEN, E>(tq, s)] = cscale<T>(v[s], scale);
+        return;
+    }
+#pragma unroll
+    for (int s = 0; s < E; ++s) v[s] = cmul<T>(v[s], sp[idx_e<LEN, E>(tq, s)]);
+    __syncthreads();  // the forward transform's last shared-memory reads are done
+    cta_fft<T, LEN, 1, E, true>(sm, v, tq, 0, tw);
+#pragma unroll
+    for (int s = 0; s < E; ++s) w[idx_r0<LEN, E>(tq, s)] = v[s];
+}
+
+// Word type for COLS output bits.
+template <int COLS> struct BitsWord;
+template <> struct BitsWord<8> { using type = uint8_t; };
+template <> struct BitsWord<16> { using type = uint16_t; };
+template <> struct BitsWord<32> { using type = uint32_t; };
+
+__device__ __forceinline__ float margin_to_float(float x) { return x; }
+__device__ __forceinline__ float margin_to_float(double x) { return __double2float_ru(x); }
+
+// Level-1 inverse pass with the post-processing of the paper's Fig. 2
+// ("rounds the result of IFFT to Boolean sequence"): round, mod 2, pack.
+// Output bit i = element i of the convolution window; bits >= m are written 0.
+// Each key's rounding margin max |w - rint(w)| goes to margin_bits (float bits,
+// atomicMax; all margins are >= 0 so integer order equals float order).
+template <typename T, int LEN, int COLS, int E>
+__global__ void __launch_bounds__(COLS * LEN / E)
+    k_inv_bits(const cx<T> *__restrict__ W, uint64_t L, uint64_t m, uint32_t nkeys,
+               const uint32_t *__restrict__ popc, uint32_t *__restrict__ margin_bits, uint64_t *__restrict__ out,
+               uint64_t ostride, TwTab<T> tw) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T> *sm = reinterpret_cast<cx<T> *>(smem_raw);
+    using word_t = typename BitsWord<COLS>::type;
+    const uint32_t col = threadIdx.x % COLS, tq = threadIdx.x / COLS;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t S = L >> ilog2(LEN);
+    const uint64_t u0 = (uint64_t)blockIdx.x * COLS;
+    const uint64_t u = u0 + col;
+    const uint32_t pair = blockIdx.y;
+    const uint32_t ka = 2 * pair, kb = 2 * pair + 1;
+    const bool has_b = kb < nkeys;
+    const cx<T> *w = W + (uint64_t)pair * L;
+    cx<T> v[E];
+#pragma unroll
+    for (int s = 0; s < E; ++s) v[s] = w[(uint64_t)idx_e<LEN, E>(tq, s) * S + u];
+    twiddle_chain<T, true, E>(v, tw, (uint32_t)(tq * u), (uint32_t)((LEN / E) * u));
+    cta_fft<T, LEN, COLS, E, true>(sm, v, tq, col, tw);
+
+    const T pa4 = (T)(popc[ka] & 3u);
+    const T pb4 = has_b ? (T)(popc[kb] & 3u) : (T)0;
+    word_t *oa = reinterpret_cast<word_t *>(out + (uint64_t)ka * ostride);
+    word_t *ob = reinterpret_cast<word_t *>(out + (uint64_t)kb * ostride);
+    const uint64_t nchunks = ((m + 63) >> 6) * (64 / COLS);
+    T ma = 0, mb = 0;
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+        const uint64_t t1 = idx_r0<LEN, E>(tq, s);
+        const uint64_t i = t1 * S + u;
+        const bool valid = i < m;
+        const T wa = (pa4 - v[s].x) * (T)0.5, wb = (pb4 - v[s].y) * (T)0.5;
+        const T ra = rint(wa), rb = rint(wb);
+        const bool bit_a = valid && (((long long)ra) & 1);
+        const bool bit_b = valid && (((long long)rb) & 1);
+        if (valid) {
+            ma = fmax(ma, fabs(wa - ra));
+            mb = fmax(mb, fabs(wb - rb));
+        }
+        const uint32_t ba = __ballot_sync(0xffffffffu, bit_a);
+        const uint32_t bb = __ballot_sync(0xffffffffu, bit_b);
+        if (col == 0) {
+            const uint64_t ci = (t1 * S + u0) / COLS;
+            const uint32_t sh = lane;  // lane = group * COLS
+            const uint32_t msk = (COLS == 32) ? 0xffffffffu : ((1u << COLS) - 1u);
+            if (ci < nchunks) {
+                oa[ci] = (word_t)((ba >> sh) & msk);
+                if (has_b) ob[ci] = (word_t)((bb >> sh) & msk);
+            }
+        }
+    }
+    uint32_t fa = __float_as_uint(margin_to_float(ma)), fb = __float_as_uint(margin_to_float(mb));
+    fa = __reduce_max_sync(0xffffffffu, fa);
+    fb = __reduce_max_sync(0xffffffffu, fb);
+    if (lane == 0) {
+        atomicMax(margin_bits + ka, fa);
+        if (has_b) atomicMax(margin_bits + kb, fb);
+    }
+}
+
+}  // namespace pa

@@ -1,0 +1,50 @@
+// pa_launch.h -- host-side launchers of the pass kernels (declarations).
+//
+// Each launcher picks the kernel instance for the pass length 2^lgLEN,
+// sets its dynamic shared memory and launches it on the given stream. The
+// definitions live in pa_launch.cuh and are instantiated once per arithmetic
+// type (pa_f32.cu for float, pa_f64.cu for double).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "fft_core.cuh"
+
+namespace pa {
+
+// Per-type kernel shape: E complex values per thread, COLS columns per CTA in
+// the strided passes. FP64 halves both to keep registers and shared memory
+// within one SM's budget.
+template <typename T> struct Shape;
+template <> struct Shape<float> { static constexpr int E = 16, COLS = 16; };
+template <> struct Shape<double> { static constexpr int E = 8, COLS = 8; };
+
+// Supported pass lengths (log2).
+constexpr int kMinLgStrided = 6, kMaxLgStrided = 10;
+template <typename T> struct MaxLgMiddle;
+template <> struct MaxLgMiddle<float> { static constexpr int v = 14; };
+template <> struct MaxLgMiddle<double> { static constexpr int v = 13; };
+constexpr int kMinLgMiddle = 6;
+
+cudaError_t launch_prep(const uint64_t *keys, uint32_t nkeys, uint64_t kstride, uint64_t n, uint32_t *popc,
+                        uint32_t *margin_bits, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_fwd_keys(int lgLEN, const uint64_t *keys, uint32_t nkeys, uint64_t kstride, uint64_t n,
+                            cx<T> *W, uint64_t L, uint32_t pairs, TwTab<T> tw, cudaStream_t st);
+template <typename T>
+cudaError_t launch_fwd_seed(int lgLEN, const uint64_t *seed, uint64_t n, uint64_t m, cx<T> *W, uint64_t L,
+                            TwTab<T> tw, cudaStream_t st);
+template <typename T>
+cudaError_t launch_mid(int lgLEN, bool inverse, cx<T> *W, uint64_t L, uint32_t lgS, uint32_t pairs, TwTab<T> tw,
+                       cudaStream_t st);
+template <typename T>
+cudaError_t launch_middle(int lgLEN, int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pairs, TwTab<T> tw,
+                          T scale, cudaStream_t st);
+template <typename T>
+cudaError_t launch_inv_bits(int lgLEN, const cx<T> *W, uint64_t L, uint64_t m, uint32_t nkeys,
+                            const uint32_t *popc, uint32_t *margin_bits, uint64_t *out, uint64_t ostride,
+                            uint32_t pairs, TwTab<T> tw, cudaStream_t st);
+
+}  // namespace pa

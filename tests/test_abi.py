@@ -1,0 +1,42 @@
+"""The C-ABI library builds, loads without a GPU and exports every declared symbol."""
+import ctypes
+import os
+import re
+
+from paper_1809_07592_gb300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(pa_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_boundary():
+    names = declared_functions()
+    for required in ["pa_plan", "pa_plan_destroy", "pa_set_seed", "pa_hash_batch", "pa_strerror"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    lib.pa_strerror.restype = ctypes.c_char_p
+    assert lib.pa_strerror(0).startswith(b"PA_OK")
+    assert lib.pa_strerror(-1).startswith(b"PA_EINVAL")
+
+
+def test_no_library_fft_or_blas_linked():
+    """The product links no cuFFT/cuBLAS: check the dynamic dependencies of libpa.so."""
+    path = build.build()
+    import subprocess
+    deps = subprocess.run(["ldd", path], capture_output=True, text=True).stdout
+    assert "cufft" not in deps and "cublas" not in deps

@@ -1,0 +1,177 @@
+"""CUDA path vs the CPU oracle, bit for bit, through the C ABI (libpa.so)."""
+import numpy as np
+import pytest
+import torch
+
+import paper_1809_07592_gb300 as pa
+from oracle import oracle
+from paper_1809_07592_gb300 import inputs
+from tests.gpu_util import sample_rows, to_dev, to_host, unpack_rows
+
+pytestmark = pytest.mark.gpu
+
+MODES = [pa.PA_FP32_GUARD, pa.PA_FP64]
+MODE_ID = {pa.PA_FP32_GUARD: "fp32g", pa.PA_FP64: "fp64"}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1809_07592_gb300 import build
+    build.build()
+    pa.lib()
+
+
+def run(n, m, dtype, keys_np, seed_np, info=True, guard=None):
+    plan = pa.Plan(n, m, dtype)
+    if guard is not None:
+        pa.pa_plan_set_guard(plan.handle, guard)
+    plan.set_seed(to_dev(seed_np)[0])
+    keys = to_dev(keys_np)
+    out, (marg, mode, esc) = plan.hash(keys, info=True)
+    torch.cuda.synchronize()
+    res = to_host(out, (m + 63) // 64)
+    shape = plan.shape()
+    plan.close()
+    return res, np.array(marg), np.array(mode), esc, shape
+
+
+# (n, m): tiny, ragged word tails, several tiles, the smallest and the two-level sizes
+SMALL = [(1, 1), (2, 1), (63, 17), (64, 64), (65, 3), (1000, 999), (4095, 1), (5000, 1500), (20000, 20000),
+         (65536, 6554), (131072, 32768), (100003, 40001), (300000, 30000)]
+
+
+@pytest.mark.parametrize("dtype", MODES, ids=MODE_ID.get)
+@pytest.mark.parametrize("n,m", SMALL)
+def test_single_key_bit_exact(n, m, dtype):
+    key, seed = inputs.block_inputs(n, m, base_seed=n * 7 + m)
+    got, marg, mode, esc, _ = run(n, m, dtype, key[None, :], seed)
+    exp = oracle.toeplitz_hash(n, m, seed, key)
+    np.testing.assert_array_equal(got[0], exp)
+    assert marg[0] < 0.05 and esc == 0 and mode[0] == dtype
+
+
+@pytest.mark.parametrize("dtype", MODES, ids=MODE_ID.get)
+@pytest.mark.parametrize("nkeys", [1, 2, 3, 7, 16])
+def test_shared_seed_batch(nkeys, dtype):
+    n, m = 40000, 9000
+    seed = inputs.bernoulli_bits(5, 1, n + m - 1)
+    keys = inputs.batch_keys(n, nkeys, base_seed=5)
+    got, marg, mode, esc, _ = run(n, m, dtype, keys, seed)
+    for k in range(nkeys):
+        np.testing.assert_array_equal(got[k], oracle.toeplitz_hash(n, m, seed, keys[k]), err_msg=f"key {k}")
+    assert esc == 0 and (marg < 0.05).all()
+
+
+def test_tail_bits_ignored_and_output_tail_zero():
+    n, m = 1000, 700
+    key, seed = inputs.block_inputs(n, m, base_seed=3)
+    k2, s2 = key.copy(), seed.copy()
+    k2[-1] |= np.uint64(0xFFFFFFFFFFFFFFFF) << np.uint64(n % 64)
+    s2[-1] |= np.uint64(0xFFFFFFFFFFFFFFFF) << np.uint64((n + m - 1) % 64)
+    exp = oracle.toeplitz_hash(n, m, seed, key)
+    for dtype in MODES:
+        plan = pa.Plan(n, m, dtype)
+        plan.set_seed(to_dev(s2)[0])
+        keys = to_dev(np.stack([k2, k2]), stride=20)
+        out = torch.full((2, 16), -1, dtype=torch.int64, device="cuda")  # padding words must stay untouched
+        plan.hash(keys, out=out)
+        torch.cuda.synchronize()
+        o = out.cpu().numpy().view(np.uint64)
+        nw = (m + 63) // 64
+        for k in range(2):
+            np.testing.assert_array_equal(o[k, :nw], exp)
+            assert int(o[k, nw - 1]) >> (m % 64) == 0
+            assert (o[k, nw:] == np.uint64(0xFFFFFFFFFFFFFFFF)).all()
+        plan.close()
+
+
+def test_forced_escalation_keeps_bits():
+    """Guard threshold below every margin: each key goes through the FP64 recomputation."""
+    n, m = 30000, 12000
+    seed = inputs.bernoulli_bits(9, 1, n + m - 1)
+    keys = inputs.batch_keys(n, 3, base_seed=9)
+    got, marg, mode, esc, _ = run(n, m, pa.PA_FP32_GUARD, keys, seed, guard=-1.0)
+    assert esc == 3 and (mode == pa.PA_FP64).all()
+    for k in range(3):
+        np.testing.assert_array_equal(got[k], oracle.toeplitz_hash(n, m, seed, keys[k]))
+
+
+@pytest.mark.parametrize("dtype", MODES, ids=MODE_ID.get)
+def test_result_independent_of_batch_mates(dtype):
+    """A key's bits do not depend on the key sharing its complex transform."""
+    n, m = 50000, 20000
+    seed = inputs.bernoulli_bits(4, 1, n + m - 1)
+    keys = inputs.batch_keys(n, 4, base_seed=4)
+    alone, *_ = run(n, m, dtype, keys[1:2], seed)
+    mixed, *_ = run(n, m, dtype, keys, seed)
+    np.testing.assert_array_equal(alone[0], mixed[1])
+
+
+@pytest.mark.parametrize("dtype", MODES, ids=MODE_ID.get)
+def test_every_pass_length(dtype):
+    """Walk L = 2^12 .. 2^22 so every two-level split and kernel instance runs once."""
+    for lgL in range(12, 23):
+        n = (1 << (lgL - 1)) + 17
+        m = max(1, (1 << lgL) - n - 5) if (1 << lgL) - n > 6 else 1
+        key, seed = inputs.block_inputs(n, m, base_seed=lgL)
+        got, marg, *_ , shape = run(n, m, dtype, key[None, :], seed)
+        assert shape[0] == 1 << lgL
+        rows = sample_rows(m, 300, seed=lgL)
+        exp = oracle.toeplitz_rows(n, m, seed, key, rows)
+        np.testing.assert_array_equal(unpack_rows(got, m)[0][rows.astype(np.int64)], exp, err_msg=f"lgL={lgL}")
+
+
+@pytest.mark.parametrize("dtype", MODES, ids=MODE_ID.get)
+def test_three_level_plan(dtype):
+    """Sizes beyond one CTA's innermost transform use the three-pass split."""
+    lgL = 25 if dtype == pa.PA_FP32_GUARD else 24
+    n = (1 << (lgL - 1)) + 1000
+    m = (1 << (lgL - 2)) - 3
+    key, seed = inputs.block_inputs(n, m, base_seed=77)
+    got, marg, mode, esc, shape = run(n, m, dtype, key[None, :], seed)
+    assert shape[3] > 1
+    rows = sample_rows(m, 200, seed=1)
+    exp = oracle.toeplitz_rows(n, m, seed, key, rows)
+    np.testing.assert_array_equal(unpack_rows(got, m)[0][rows.astype(np.int64)], exp)
+    assert marg[0] < 0.1
+
+
+@pytest.mark.parametrize("n", [1_000_000, 1 << 20])
+@pytest.mark.parametrize("ratio", [0.1, 0.25, 0.5])
+def test_dv_qkd_block_64_keys(n, ratio):
+    """64 keys sharing one seed at the DV-QKD block sizes; FP32-guarded, sampled rows vs the oracle."""
+    m = int(ratio * n)
+    seed = inputs.bernoulli_bits(0, 1, n + m - 1)
+    keys = inputs.batch_keys(n, 64, base_seed=0)
+    got, marg, mode, esc, _ = run(n, m, pa.PA_FP32_GUARD, keys, seed)
+    assert esc == 0 and (marg < 0.05).all()
+    bits = unpack_rows(got[[0, 1, 31, 62, 63]], m)
+    rows = sample_rows(m, 150, seed=n)
+    for j, k in enumerate([0, 1, 31, 62, 63]):
+        exp = oracle.toeplitz_rows(n, m, seed, keys[k], rows)
+        np.testing.assert_array_equal(bits[j][rows.astype(np.int64)], exp, err_msg=f"key {k}")
+
+
+def test_argument_errors():
+    with pytest.raises(pa.PAError):
+        pa.pa_plan(10, 11, pa.PA_FP64)  # m > n
+    with pytest.raises(pa.PAError):
+        pa.pa_plan(0, 0, pa.PA_FP64)
+    plan = pa.Plan(1000, 100, pa.PA_FP32_GUARD)
+    keys = torch.zeros((2, 16), dtype=torch.int64, device="cuda")
+    out = torch.zeros((2, 2), dtype=torch.int64, device="cuda")
+    with pytest.raises(pa.PAError) as e:
+        plan.hash(keys, out=out)
+    assert e.value.code == pa.PA_ENOSEED
+    seed = torch.zeros(18, dtype=torch.int64, device="cuda")
+    with pytest.raises(pa.PAError) as e:
+        pa.pa_set_seed(plan.handle, seed, 1000)  # wrong seed length
+    assert e.value.code == pa.PA_EINVAL
+    plan.set_seed(seed)
+    with pytest.raises(pa.PAError) as e:
+        pa.pa_hash_batch(plan.handle, keys, 2, 15, out, 2)  # odd stride
+    assert e.value.code == pa.PA_EINVAL
+    with pytest.raises(pa.PAError) as e:
+        pa.pa_hash_batch(plan.handle, keys[:, 1:], 2, 16, out, 2)  # misaligned
+    assert e.value.code == pa.PA_EINVAL
+    plan.close()
