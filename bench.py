@@ -1,0 +1,418 @@
+"""Benchmark: PA input Mbit/s of the FFT Toeplitz hash on one GB300 (bit-exact path).
+
+Workload (the DV-QKD block sizes): n in {1,000,000, 2^20} input bits x
+compression m/n in {0.1, 0.25, 0.5}; for each of the six (n, m) pairs, a batch
+of 64 independent keys that share one Toeplitz seed (its spectrum cached on the
+device). One step hashes all six batches, FP32 transforms with the per-key
+rounding guard (escalating to FP64 when the margin exceeds 0.25). Inputs are
+i.i.d. Bernoulli(0.5) bits (SplitMix64, seed 0), already resident in HBM.
+
+Reported beside the headline: the plain single-key FP64 form on the same
+sizes, p50/p99 batch latency, the dominant kernel's roofline, an end-to-end
+number through host buffers, and the CPU oracle on a bounded sample.
+
+``--impl reference`` times the CPU oracle instead (the reference arm).
+Under torchrun (N > 1) every rank hashes its own batches (replicas; the path
+has no exchange step) and rank 0 prints the whole-job number.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "dv_qkd_64keys_shared_seed"
+N_VALUES = (1_000_000, 1 << 20)
+RATIOS = (0.1, 0.25, 0.5)
+NKEYS = 64
+METRIC = "PA input Mbit/s per GB300 (bit-exact), batched/FP32 vs plain FP64; p50/p99 block latency"
+
+
+def subconfigs():
+    return [(n, int(r * n)) for n in N_VALUES for r in RATIOS]
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1809_07592_gb300", "csrc", "*"))):
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if its source hash is current."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{WORKLOAD}.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for ln in open(path):
+        if ":" in ln and ln.strip().startswith("- "):
+            k, v = ln.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_hash") != source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_full"])
+    except (KeyError, ValueError):
+        return None
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def algorithmic_bytes(kind: str, n: int, m: int, L: int, pairs: int, nkeys: int, elem: int) -> float:
+    """Compulsory bytes one launch of a kernel family moves (complex work slot = L * elem bytes per pair)."""
+    slot = L * elem
+    kw, ow = (n + 63) // 64 * 8, (m + 63) // 64 * 8
+    if kind == "fwd_keys":
+        return pairs * slot + nkeys * kw
+    if kind == "middle_conv":
+        return 2 * pairs * slot + slot  # W in, W out, seed spectrum once
+    if kind == "inv_bits":
+        return pairs * slot + nkeys * ow
+    if kind in ("mid_fwd", "mid_inv"):
+        return 2 * pairs * slot
+    if kind == "prep":
+        return nkeys * kw
+    return 0.0
+
+
+def cpu_baseline(budget_s: float = 12.0):
+    """The oracle, as it stands, on a bounded sample: rows of key 0 of (n=2^20, m=n/4), scaled to a whole key."""
+    from oracle import oracle
+    from paper_1809_07592_gb300 import inputs
+    n, m = 1 << 20, 1 << 18
+    key, seed = inputs.block_inputs(n, m, base_seed=0, key_stream=2)
+    threads = os.cpu_count() or 1
+    rows = 1024
+    t0 = time.perf_counter()
+    oracle.toeplitz_row_range(n, m, seed, key, 0, rows, threads)
+    dt = time.perf_counter() - t0
+    rows = int(min(m, max(rows, rows * budget_s / max(dt, 1e-6))))
+    rows -= rows % 64
+    t0 = time.perf_counter()
+    oracle.toeplitz_row_range(n, m, seed, key, 0, rows, threads)
+    dt = time.perf_counter() - t0
+    per_key = dt * m / rows
+    return {"value": n / per_key / 1e6, "unit": "Mbit/s", "cores": threads, "kind": "oracle",
+            "sample": f"key 0 of n=1048576, m=262144: rows 0..{rows - 1} of {m} in {dt:.2f} s, scaled to all rows",
+            "seconds": round(dt, 3)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import oracle
+    from paper_1809_07592_gb300 import inputs
+    threads = os.cpu_count() or 1
+    n, m = 1 << 20, 1 << 18
+    key, seed = inputs.block_inputs(n, m, base_seed=0, key_stream=2)
+    rows = 4096
+    oracle.toeplitz_row_range(n, m, seed, key, 0, 256, threads)  # build + warm
+    for _ in range(args.warmup):
+        oracle.toeplitz_row_range(n, m, seed, key, 0, 256, threads)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.toeplitz_row_range(n, m, seed, key, 0, rows, threads)
+        times.append((time.perf_counter() - t0) * m / rows)  # seconds per whole key
+    per_key = statistics.median(times)
+    value = n / per_key / 1e6
+    line = {"metric": METRIC, "value": value, "unit": "Mbit/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per_key * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "one key of n=1048576, m=262144 per step"},
+            "impl": "reference",
+            "cpu_baseline": {"kind": "oracle", "cores": threads, "value": value, "unit": "Mbit/s",
+                             "sample": f"rows 0..{rows - 1} of key 0 (n=1048576, m=262144) per step, "
+                                       f"scaled to all {m} rows"},
+            "e2e": {"value": value, "unit": "Mbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import paper_1809_07592_gb300 as pa
+    from paper_1809_07592_gb300 import inputs
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    pa.lib()
+
+    # --- inputs resident in HBM; one plan + seed per (n, m) -------------------------------------------
+    cases = []
+    base = 1000 * rank  # each replica draws its own keys
+    for n, m in subconfigs():
+        seed = inputs.bernoulli_bits(base, inputs.STREAM_SEED, n + m - 1)
+        keys = inputs.batch_keys(n, NKEYS, base_seed=base)
+        kw = keys.shape[1] + (keys.shape[1] & 1)
+        kb = np.zeros((NKEYS, kw), np.uint64)
+        kb[:, : keys.shape[1]] = keys
+        sw = np.zeros(seed.size + (seed.size & 1), np.uint64)
+        sw[: seed.size] = seed
+        ow = (m + 63) // 64
+        ow += ow & 1
+        plan = pa.Plan(n, m, pa.PA_FP32_GUARD)
+        plan.set_seed(torch.from_numpy(sw.view(np.int64)).to(dev))
+        dk = torch.from_numpy(kb.view(np.int64)).to(dev)
+        out = torch.empty((NKEYS, ow), dtype=torch.int64, device=dev)
+        hk = torch.from_numpy(kb.view(np.int64)).pin_memory()
+        ho = torch.empty((NKEYS, ow), dtype=torch.int64).pin_memory()
+        cases.append(dict(n=n, m=m, plan=plan, dk=dk, out=out, hk=hk, ho=ho, kw=kw, ow=ow, seed_dev=sw))
+    L = cases[0]["plan"].shape()[0]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        lat = []
+        for c in cases:
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pa.pa_hash_batch(c["plan"].handle, c["dk"], NKEYS, c["kw"], c["out"], c["ow"], stream)
+            b.record(stream)
+            lat.append((a, b))
+        return lat
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    for c in cases:
+        pa.pa_profile_enable(c["plan"].handle, True)
+        pa.pa_profile_read(c["plan"].handle, reset=True)
+
+    step_ms, lat_ms = [], []
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        for _ in range(args.steps):
+            flush.zero_()
+            barrier()
+            s0 = torch.cuda.Event(enable_timing=True)
+            s1 = torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            lat = step()
+            s1.record(stream)
+            torch.cuda.synchronize()
+            step_ms.append(s0.elapsed_time(s1))
+            lat_ms += [a.elapsed_time(b) for a, b in lat]
+    barrier()
+
+    # per-kernel live timings over the timed region
+    prof = {}
+    for c in cases:
+        for k, (cnt, ms) in pa.pa_profile_read(c["plan"].handle, reset=True).items():
+            pc = prof.setdefault(k, [0, 0.0, 0.0])
+            pc[0] += cnt
+            pc[1] += ms
+            if cnt:
+                shape = c["plan"].shape()
+                pc[2] += cnt * algorithmic_bytes(k, c["n"], c["m"], shape[0], NKEYS // 2, NKEYS, 8)
+        pa.pa_profile_enable(c["plan"].handle, False)
+    gpu_launches = int(sum(v[0] for v in prof.values()))
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    dom_name, (dom_cnt, dom_ms, dom_bytes) = dom
+    avg_ms = dom_ms / dom_cnt
+    achieved = (dom_bytes / dom_cnt) / (avg_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = ncu_traffic(dom_name)
+
+    bits_per_step = sum(c["n"] for c in cases) * NKEYS
+    t_step = statistics.mean(step_ms)
+    total = torch.tensor([t_step], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(total, op=dist.ReduceOp.MAX)
+    t_max = float(total.item())
+    value = bits_per_step * world / (t_max * 1e-3) / 1e6
+
+    # --- plain single-key FP64 form on the same sizes (the other side of the metric) ---------------
+    fp64 = []
+    for c in cases:
+        p64 = pa.Plan(c["n"], c["m"], pa.PA_FP64)
+        p64.set_seed(torch.from_numpy(c["seed_dev"].view(np.int64)).to(dev))
+        o1 = torch.empty((1, c["ow"]), dtype=torch.int64, device=dev)
+        pa.pa_hash_batch(p64.handle, c["dk"][0:1], 1, c["kw"], o1, c["ow"])
+        torch.cuda.synchronize()
+        ts = []
+        for k in range(4):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pa.pa_hash_batch(p64.handle, c["dk"][k:k + 1], 1, c["kw"], o1, c["ow"])
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        fp64.append((c["n"], statistics.median(ts)))
+        p64.close()
+    fp64_value = sum(n for n, _ in fp64) / (sum(t for _, t in fp64) * 1e-3) / 1e6
+
+    # --- end to end through host buffers (pinned H2D of keys, hash, D2H of final keys) ---------------
+    h2d = sum(c["hk"].numel() * 8 for c in cases)
+    d2h = sum(c["ho"].numel() * 8 for c in cases)
+    e2e_ms = []
+    for it in range(args.warmup + args.steps):
+        flush.zero_()
+        barrier()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for c in cases:
+            c["dk"].copy_(c["hk"], non_blocking=True)
+            pa.pa_hash_batch(c["plan"].handle, c["dk"], NKEYS, c["kw"], c["out"], c["ow"], stream)
+            c["ho"].copy_(c["out"], non_blocking=True)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            e2e_ms.append(s0.elapsed_time(s1))
+    te = torch.tensor([statistics.mean(e2e_ms)], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = bits_per_step * world / (float(te.item()) * 1e-3) / 1e6
+
+    if rank == 0:
+        lat_sorted = sorted(lat_ms)
+        p50 = float(np.percentile(lat_sorted, 50))
+        p99 = float(np.percentile(lat_sorted, 99))
+        line = {
+            "metric": METRIC, "value": value, "unit": "Mbit/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": list(N_VALUES), "m_over_n": list(RATIOS), "keys_per_batch": NKEYS,
+                       "batches_per_step": len(cases), "mode": "FP32_GUARD", "transform_length": L,
+                       "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas{world}"},
+            "latency_ms": {"p50": p50, "p99": p99, "unit": "ms per 64-key batch"},
+            "fp64_plain": {"value": fp64_value, "unit": "Mbit/s",
+                           "form": "single key per call, FP64 transforms, same (n, m) set"},
+            "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+                         "avg_launch_ms": avg_ms, "launches": dom_cnt},
+            "kernels": {k: {"launches": v[0], "avg_ms": v[1] / v[0] if v[0] else None,
+                            "achieved_gbs": (v[2] / v[0]) / (v[1] / v[0] * 1e-3) / 1e9 if v[0] else None}
+                        for k, v in prof.items() if v[0]},
+            "gpu_launches": gpu_launches,
+            "e2e": {"value": e2e_value, "unit": "Mbit/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "clocks": clocks.summary(),
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line))
+    for c in cases:
+        c["plan"].close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

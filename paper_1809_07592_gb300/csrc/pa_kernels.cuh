@@ -31,6 +31,20 @@
 
 namespace pa {
 
+// Resident CTAs requested per SM for a CTA of `threads` threads: enough for 1024
+// threads, so the register allocation stays <= 64 per thread and at least two
+// CTAs overlap their load, transform and store phases.
+__host__ __device__ constexpr int min_blocks(int threads) { return threads >= 1024 ? 1 : (1024 / threads > 16 ? 16 : 1024 / threads); }
+
+// Rounding to the nearest integer (ties to even) by adding and subtracting
+// 1.5 * 2^(mantissa bits): exact for |x| < 2^22 (float) / 2^51 (double); the
+// integer's parity is the lowest bit of the sum's encoding.
+template <typename T> struct Magic;
+template <> struct Magic<float> { static constexpr float v = 12582912.0f, limit = 2097152.0f; };
+template <> struct Magic<double> { static constexpr double v = 6755399441055744.0, limit = 1125899906842624.0; };
+__device__ __forceinline__ uint32_t low_bit(float x) { return __float_as_uint(x) & 1u; }
+__device__ __forceinline__ uint32_t low_bit(double x) { return (uint32_t)__double_as_longlong(x) & 1u; }
+
 // ---------------------------------------------------------------------------
 // popcount P of each key (bits < n) and reset of its rounding margin.
 __global__ void k_prep(const uint64_t *__restrict__ keys, uint32_t nkeys, uint64_t kstride, uint64_t n,
@@ -40,7 +54,7 @@ __global__ void k_prep(const uint64_t *__restrict__ keys, uint32_t nkeys, uint64
 // Level-1 forward pass from packed key bits. Grid (S/COLS, pairs); pair p
 // carries key 2p in the real part and key 2p+1 (if any) in the imaginary part.
 template <typename T, int LEN, int COLS, int E>
-__global__ void __launch_bounds__(COLS * LEN / E)
+__global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
     k_fwd_keys(const uint64_t *__restrict__ keys, uint32_t nkeys, uint64_t kstride, uint64_t n,
                cx<T> *__restrict__ W, uint64_t L, TwTab<T> tw) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -49,19 +63,23 @@ __global__ void __launch_bounds__(COLS * LEN / E)
     const uint64_t S = L >> ilog2(LEN);
     const uint64_t u = (uint64_t)blockIdx.x * COLS + col;
     const uint32_t pair = blockIdx.y;
-    const uint64_t *ka = keys + (uint64_t)(2 * pair) * kstride;
     const bool has_b = 2 * pair + 1 < nkeys;
-    const uint64_t *kb = keys + (uint64_t)(2 * pair + (has_b ? 1 : 0)) * kstride;
+    // S is a multiple of 64, so bit a*S + u lies in word a*(S/64) + u/64 at position u % 64.
+    const uint64_t S64 = S >> 6;
+    const uint32_t sh = (uint32_t)(u & 63);
+    const uint64_t *ka = keys + (uint64_t)(2 * pair) * kstride + (u >> 6);
+    const uint64_t *kb = keys + (uint64_t)(2 * pair + (has_b ? 1 : 0)) * kstride + (u >> 6);
+    const uint64_t arows = n > u ? (n - u + S - 1) / S : 0;  // rows a with a*S + u < n
     cx<T> v[E];
 #pragma unroll
     for (int s = 0; s < E; ++s) {
-        const uint64_t t = (uint64_t)idx_r0<LEN, E>(tq, s) * S + u;
-        T xa = 0, xb = 0;
-        if (t < n) {
-            xa = (T)((__ldg(ka + (t >> 6)) >> (t & 63)) & 1u);
-            if (has_b) xb = (T)((__ldg(kb + (t >> 6)) >> (t & 63)) & 1u);
+        const uint32_t a = idx_r0<LEN, E>(tq, s);
+        uint32_t ba = 0, bb = 0;
+        if (a < arows) {
+            ba = (uint32_t)(__ldg(ka + a * S64) >> sh) & 1u;
+            if (has_b) bb = (uint32_t)(__ldg(kb + a * S64) >> sh) & 1u;
         }
-        v[s] = mk<T>(xa, xb);
+        v[s] = mk<T>(ba ? (T)1 : (T)0, bb ? (T)1 : (T)0);
     }
     cta_fft<T, LEN, COLS, E, false>(sm, v, tq, col, tw);
     cx<T> *w = W + (uint64_t)pair * L;
@@ -73,7 +91,7 @@ __global__ void __launch_bounds__(COLS * LEN / E)
 
 // Level-1 forward pass of the rotated, +-1 encoded seed (real input).
 template <typename T, int LEN, int COLS, int E>
-__global__ void __launch_bounds__(COLS * LEN / E)
+__global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
     k_fwd_seed(const uint64_t *__restrict__ seed, uint64_t n, uint64_t m, cx<T> *__restrict__ W, uint64_t L,
                TwTab<T> tw) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -101,7 +119,7 @@ __global__ void __launch_bounds__(COLS * LEN / E)
 // Middle-level strided pass (three-level plans only), forward or inverse.
 // Grid (S/COLS, blocks * pairs) with blocks = L / (LEN * S).
 template <typename T, int LEN, int COLS, int E, bool INV>
-__global__ void __launch_bounds__(COLS * LEN / E)
+__global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
     k_mid(cx<T> *__restrict__ W, uint64_t L, uint32_t lgS, TwTab<T> tw) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T> *sm = reinterpret_cast<cx<T> *>(smem_raw);
@@ -173,7 +191,7 @@ __device__ __forceinline__ float margin_to_float(double x) { return __double2flo
 // Each key's rounding margin max |w - rint(w)| goes to margin_bits (float bits,
 // atomicMax; all margins are >= 0 so integer order equals float order).
 template <typename T, int LEN, int COLS, int E>
-__global__ void __launch_bounds__(COLS * LEN / E)
+__global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
     k_inv_bits(const cx<T> *__restrict__ W, uint64_t L, uint64_t m, uint32_t nkeys,
                const uint32_t *__restrict__ popc, uint32_t *__restrict__ margin_bits, uint64_t *__restrict__ out,
                uint64_t ostride, TwTab<T> tw) {
@@ -207,12 +225,13 @@ __global__ void __launch_bounds__(COLS * LEN / E)
         const uint64_t i = t1 * S + u;
         const bool valid = i < m;
         const T wa = (pa4 - v[s].x) * (T)0.5, wb = (pb4 - v[s].y) * (T)0.5;
-        const T ra = rint(wa), rb = rint(wb);
-        const bool bit_a = valid && (((long long)ra) & 1);
-        const bool bit_b = valid && (((long long)rb) & 1);
+        const T fa = wa + Magic<T>::v, fb = wb + Magic<T>::v;  // rint via the 1.5*2^p addition
+        const bool bit_a = valid && low_bit(fa);
+        const bool bit_b = valid && low_bit(fb);
         if (valid) {
-            ma = fmax(ma, fabs(wa - ra));
-            mb = fmax(mb, fabs(wb - rb));
+            // beyond 2^21 (float) the parity is not resolvable: report a margin of 1 so the guard escalates
+            ma = fmax(ma, fabs(wa) < Magic<T>::limit ? fabs(wa - (fa - Magic<T>::v)) : (T)1);
+            mb = fmax(mb, fabs(wb) < Magic<T>::limit ? fabs(wb - (fb - Magic<T>::v)) : (T)1);
         }
         const uint32_t ba = __ballot_sync(0xffffffffu, bit_a);
         const uint32_t bb = __ballot_sync(0xffffffffu, bit_b);

@@ -96,6 +96,23 @@ def test_forced_escalation_keeps_bits():
         np.testing.assert_array_equal(got[k], oracle.toeplitz_hash(n, m, seed, keys[k]))
 
 
+@pytest.mark.parametrize("n,m", [(1 << 20, 1 << 18), (1 << 23, 1 << 21)])
+def test_adversarial_all_ones_escalates_or_exact(n, m):
+    """All-ones key and seed make |w| ~ n/2: FP32 cannot resolve it and must hand the keys to FP64."""
+    ones_k = inputs.mask_tail(np.full((n + 63) // 64, 0xFFFFFFFFFFFFFFFF, dtype=np.uint64), n)
+    ones_s = inputs.mask_tail(np.full((n + m + 62) // 64, 0xFFFFFFFFFFFFFFFF, dtype=np.uint64), n + m - 1)
+    rnd = inputs.bernoulli_bits(1, 2, n)
+    keys = np.stack([ones_k, rnd])
+    got, marg, mode, esc, _ = run(n, m, pa.PA_FP32_GUARD, keys, ones_s)
+    assert mode[0] == pa.PA_FP64 and esc >= 1
+    rows = sample_rows(m, 100)
+    for k in range(2):
+        exp = oracle.toeplitz_rows(n, m, ones_s, keys[k], rows)
+        np.testing.assert_array_equal(unpack_rows(got, m)[k][rows.astype(np.int64)], exp)
+    # all-ones seed: every output bit is the key's popcount parity
+    assert (unpack_rows(got, m)[0] == (n & 1)).all()
+
+
 @pytest.mark.parametrize("dtype", MODES, ids=MODE_ID.get)
 def test_result_independent_of_batch_mates(dtype):
     """A key's bits do not depend on the key sharing its complex transform."""
