@@ -19,25 +19,17 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace pa {
 
-template <typename T> struct Vec2;
-template <> struct Vec2<float> { using type = float2; };
-template <> struct Vec2<double> { using type = double2; };
-template <typename T> using cx = typename Vec2<T>::type;
-
-template <typename T> __device__ __forceinline__ cx<T> mk(T x, T y) { cx<T> r; r.x = x; r.y = y; return r; }
-template <typename T> __device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
-template <typename T> __device__ __forceinline__ cx<T> csub(cx<T> a, cx<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
-template <typename T> __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
-    return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-template <typename T> __device__ __forceinline__ cx<T> cmulc(cx<T> a, cx<T> b) {  // a * conj(b)
-    return mk<T>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
-}
-template <typename T> __device__ __forceinline__ cx<T> cscale(cx<T> a, T s) { return mk<T>(a.x * s, a.y * s); }
+// Element arithmetic of the transforms. Arith<float> / Arith<double> work on
+// complex numbers (x = real, y = imaginary); Arith<Zp> (zp.cuh) on residues
+// modulo the prime p = 2^64 - 2^32 + 1. The FFT engine below only uses add,
+// sub, mul, the in-register roots rot32 and the table twiddles omega.
+template <typename T> struct Arith;
+template <typename T> using cx = typename Arith<T>::E;
 
 // cos(pi*j/16), j = 0..8, to 20 significant digits.
 __host__ __device__ constexpr double cos_pi16(int j) {
@@ -55,16 +47,46 @@ __host__ __device__ constexpr double cos_pi16(int j) {
 __host__ __device__ constexpr double cos32(int j) { return j <= 8 ? cos_pi16(j) : -cos_pi16(16 - j); }
 __host__ __device__ constexpr double sin32(int j) { return j <= 8 ? cos_pi16(8 - j) : cos_pi16(j - 8); }
 
-// x * w^j with w = exp(-2*pi*i/32) (forward) or its conjugate (inverse). j is a
-// compile-time constant after unrolling, so the branches fold away.
-template <typename T, bool INV>
-__device__ __forceinline__ cx<T> rot32(cx<T> x, int j) {
-    if (j == 0) return x;
-    if (j == 8) return INV ? mk<T>(-x.y, x.x) : mk<T>(x.y, -x.x);
-    const T c = (T)cos32(j);
-    const T s = INV ? (T)sin32(j) : -(T)sin32(j);
-    return mk<T>(x.x * c - x.y * s, x.x * s + x.y * c);
-}
+// Twiddle table pair for the length-L transform root w_L: w_L^e = hi[e >> B] * lo[e & (2^B-1)].
+// Complex roots are exp(-2*pi*i/L), computed in double precision on the host and rounded to T.
+template <typename T> struct TwTab {
+    const cx<T> *hi;
+    const cx<T> *lo;
+    uint32_t B;    // split position
+    uint32_t lgL;  // log2 L
+};
+
+template <typename T> struct ComplexArith {
+    using E = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+    static __device__ __forceinline__ E mk(T x, T y) { E r; r.x = x; r.y = y; return r; }
+    static __device__ __forceinline__ E add(E a, E b) { return mk(a.x + b.x, a.y + b.y); }
+    static __device__ __forceinline__ E sub(E a, E b) { return mk(a.x - b.x, a.y - b.y); }
+    static __device__ __forceinline__ E mul(E a, E b) { return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+    // x * w^j with w = exp(-2*pi*i/32) (forward) or its conjugate (inverse). j is a
+    // compile-time constant after unrolling, so the branches fold away.
+    template <bool INV> static __device__ __forceinline__ E rot32(E x, int j) {
+        if (j == 0) return x;
+        if (j == 8) return INV ? mk(-x.y, x.x) : mk(x.y, -x.x);
+        const T c = (T)cos32(j);
+        const T s = INV ? (T)sin32(j) : -(T)sin32(j);
+        return mk(x.x * c - x.y * s, x.x * s + x.y * c);
+    }
+    template <bool INV> static __device__ __forceinline__ E omega(const TwTab<T> &t, uint32_t e) {
+        E a = __ldg(t.hi + (e >> t.B));
+        E b = __ldg(t.lo + (e & ((1u << t.B) - 1u)));
+        E w = mul(a, b);
+        if (INV) w.y = -w.y;
+        return w;
+    }
+};
+template <> struct Arith<float> : ComplexArith<float> {};
+template <> struct Arith<double> : ComplexArith<double> {};
+
+}  // namespace pa
+
+#include "zp.cuh"
+
+namespace pa {
 
 __host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v >> 1); }
 __host__ __device__ constexpr int bitrev(int v, int bits) {
@@ -86,8 +108,8 @@ __device__ __forceinline__ void dft(cx<T> *v) {
 #pragma unroll
                 for (int j = 0; j < len / 2; ++j) {
                     cx<T> a = v[b + j], c = v[b + j + len / 2];
-                    v[b + j] = cadd<T>(a, c);
-                    v[b + j + len / 2] = rot32<T, INV>(csub<T>(a, c), j * (32 / len));
+                    v[b + j] = Arith<T>::add(a, c);
+                    v[b + j + len / 2] = Arith<T>::template rot32<INV>(Arith<T>::sub(a, c), j * (32 / len));
                 }
             }
         }
@@ -99,35 +121,17 @@ __device__ __forceinline__ void dft(cx<T> *v) {
     }
 }
 
-// Twiddle table pair for w_L = exp(-2*pi*i/L): w_L^e = hi[e >> B] * lo[e & (2^B-1)].
-// Entries are computed in double precision on the host and rounded to T.
-template <typename T> struct TwTab {
-    const cx<T> *hi;
-    const cx<T> *lo;
-    uint32_t B;    // split position
-    uint32_t lgL;  // log2 L
-};
-
-template <typename T, bool INV>
-__device__ __forceinline__ cx<T> omega(const TwTab<T> &t, uint32_t e) {
-    cx<T> a = __ldg(t.hi + (e >> t.B));
-    cx<T> b = __ldg(t.lo + (e & ((1u << t.B) - 1u)));
-    cx<T> w = cmul<T>(a, b);
-    if (INV) w.y = -w.y;
-    return w;
-}
-
 // v[r] *= w_L^{e0 + r*de} for r = 0..N-1: two table lookups, then a chain of
 // complex products (relative error grows by about one rounding per step).
 template <typename T, bool INV, int N>
 __device__ __forceinline__ void twiddle_chain(cx<T> *v, const TwTab<T> &tw, uint32_t e0, uint32_t de) {
-    const cx<T> g = omega<T, INV>(tw, de);
-    cx<T> w = (e0 == 0u) ? g : omega<T, INV>(tw, e0 + de);
-    if (e0 != 0u) v[0] = cmul<T>(v[0], omega<T, INV>(tw, e0));
+    const cx<T> g = Arith<T>::template omega<INV>(tw, de);
+    cx<T> w = (e0 == 0u) ? g : Arith<T>::template omega<INV>(tw, e0 + de);
+    if (e0 != 0u) v[0] = Arith<T>::mul(v[0], Arith<T>::template omega<INV>(tw, e0));
 #pragma unroll
     for (int r = 1; r < N; ++r) {
-        v[r] = cmul<T>(v[r], w);
-        if (r + 1 < N) w = cmul<T>(w, g);
+        v[r] = Arith<T>::mul(v[r], w);
+        if (r + 1 < N) w = Arith<T>::mul(w, g);
     }
 }
 

@@ -54,8 +54,10 @@ struct Shape3 {
     int lg1, lg2, lg3;  // lg3 == 0: two levels, lg2 is the innermost
 };
 
-Shape3 choose_shape(int lgL, bool fp64) {
-    const int maxMid = fp64 ? MaxLgMiddle<double>::v : MaxLgMiddle<float>::v;
+Shape3 choose_shape(int lgL, pa_dtype_t dtype) {
+    const int maxMid = dtype == PA_FP32_GUARD ? MaxLgMiddle<float>::v
+                       : dtype == PA_FP64     ? MaxLgMiddle<double>::v
+                                              : MaxLgMiddle<Zp>::v;
     Shape3 s{0, 0, 0};
     int lg1 = lgL - 12;
     if (lg1 < kMinLgStrided) lg1 = kMinLgStrided;
@@ -99,7 +101,7 @@ struct pa_plan {
     uint64_t *seed_copy = nullptr;  // the seed bits, kept for an escalation plan
     bool seeded = false;
     float guard = 0.25f;
-    pa_plan_t *fallback = nullptr;    // FP64 plan used to recompute keys that fail the FP32 guard
+    pa_plan_t *fallback = nullptr;    // next-wider plan (FP32 -> FP64 -> NTT64) for keys that fail the guard
     std::mutex mu;
     // kernel timing
     bool prof = false;
@@ -152,7 +154,35 @@ void collect_events(pa_plan_t *p) {
     p->ev_used = 0;
 }
 
-size_t elem_bytes(pa_dtype_t d) { return d == PA_FP32_GUARD ? sizeof(float2) : sizeof(double2); }
+size_t elem_bytes(pa_dtype_t d) {
+    return d == PA_FP32_GUARD ? sizeof(float2) : d == PA_FP64 ? sizeof(double2) : sizeof(uint64_t);
+}
+
+// ---- modular helpers (host) for the NTT mode -------------------------------------------------
+uint64_t zp_mul_host(uint64_t a, uint64_t b) {
+    unsigned __int128 x = (unsigned __int128)a * b;
+    return zp_reduce((uint64_t)(x >> 64), (uint64_t)x);
+}
+uint64_t zp_pow_host(uint64_t a, uint64_t e) {
+    uint64_t r = 1;
+    while (e) {
+        if (e & 1) r = zp_mul_host(r, a);
+        a = zp_mul_host(a, a);
+        e >>= 1;
+    }
+    return r;
+}
+// Root of unity of order L (a power of two, 32 <= L <= 2^32) whose L/32-th power
+// is 2^6, the root the in-register DFTs use.
+uint64_t zp_root(uint64_t L) {
+    const uint64_t g = 7;  // generates the multiplicative group mod p
+    const uint64_t w = zp_pow_host(g, (kP - 1) / L);
+    const uint64_t w32 = zp_pow_host(w, L / 32);
+    for (uint64_t j = 1; j < 64; j += 2) {
+        if (zp_pow_host(w32, j) == 64ull) return zp_pow_host(w, j);
+    }
+    return 0;
+}
 
 template <typename T>
 int build_twiddles(pa_plan_t *p) {
@@ -179,6 +209,37 @@ int build_twiddles(pa_plan_t *p) {
     p->twB = B;
     return PA_OK;
 }
+
+template <>
+int build_twiddles<Zp>(pa_plan_t *p) {
+    const int lgL = p->lgL;
+    const uint32_t B = (uint32_t)(lgL + 1) / 2;
+    const uint64_t nhi = 1ull << (lgL - B), nlo = 1ull << B;
+    std::vector<uint64_t> hi(nhi), lo(nlo);
+    const uint64_t w = zp_root(p->L);
+    if (w == 0) return PA_EUNSUPPORTED;
+    const uint64_t wB = zp_pow_host(w, 1ull << B);
+    uint64_t x = 1;
+    for (uint64_t h = 0; h < nhi; ++h) { hi[h] = x; x = zp_mul_host(x, wB); }
+    x = 1;
+    for (uint64_t l = 0; l < nlo; ++l) { lo[l] = x; x = zp_mul_host(x, w); }
+    PA_CUDA(cudaMalloc(&p->tw_hi, nhi * sizeof(uint64_t)));
+    PA_CUDA(cudaMalloc(&p->tw_lo, nlo * sizeof(uint64_t)));
+    PA_CUDA(cudaMemcpy(p->tw_hi, hi.data(), nhi * sizeof(uint64_t), cudaMemcpyHostToDevice));
+    PA_CUDA(cudaMemcpy(p->tw_lo, lo.data(), nlo * sizeof(uint64_t), cudaMemcpyHostToDevice));
+    p->twB = B;
+    return PA_OK;
+}
+
+// 1/L as the element type's scaling factor.
+template <typename T> cx<T> inv_length(uint64_t L) {
+    cx<T> s;
+    s.x = (decltype(s.x))(1.0 / (double)L);
+    s.y = 0;
+    return s;
+}
+template <> cx<Zp> inv_length<Zp>(uint64_t L) { return zp_pow_host(L, kP - 2); }
+template <typename T> cx<T> one() { return inv_length<T>(1); }
 
 template <typename T>
 TwTab<T> tw_of(const pa_plan_t *p) {
@@ -259,7 +320,7 @@ int run_seed(pa_plan_t *p, const uint64_t *seed, cudaStream_t st) {
         { Timed t_(p, K_MID_FWD, st); PA_CUDA(launch_mid<T>(s.lg2, false, W, p->L, (uint32_t)s.lg3, 1, tw, st)); }
         inner = s.lg3;
     }
-    { Timed t_(p, K_MIDDLE_SPEC, st); PA_CUDA(launch_middle<T>(inner, 1, W, spec, p->L, 1, tw, (T)(1.0 / (double)p->L), st)); }
+    { Timed t_(p, K_MIDDLE_SPEC, st); PA_CUDA(launch_middle<T>(inner, 1, W, spec, p->L, 1, tw, inv_length<T>(p->L), st)); }
     return PA_OK;
 }
 
@@ -281,10 +342,10 @@ int run_keys(pa_plan_t *p, const uint64_t *keys, uint32_t nkeys, uint64_t kstrid
         { Timed t_(p, K_FWD_KEYS, st); PA_CUDA(launch_fwd_keys<T>(s.lg1, kp, nk, kstride, p->n, W, p->L, pairs, tw, st)); }
         if (s.lg3) {
             { Timed t_(p, K_MID_FWD, st); PA_CUDA(launch_mid<T>(s.lg2, false, W, p->L, (uint32_t)s.lg3, pairs, tw, st)); }
-            { Timed t_(p, K_MIDDLE_CONV, st); PA_CUDA(launch_middle<T>(s.lg3, 0, W, spec, p->L, pairs, tw, (T)1, st)); }
+            { Timed t_(p, K_MIDDLE_CONV, st); PA_CUDA(launch_middle<T>(s.lg3, 0, W, spec, p->L, pairs, tw, one<T>(), st)); }
             { Timed t_(p, K_MID_INV, st); PA_CUDA(launch_mid<T>(s.lg2, true, W, p->L, (uint32_t)s.lg3, pairs, tw, st)); }
         } else {
-            { Timed t_(p, K_MIDDLE_CONV, st); PA_CUDA(launch_middle<T>(s.lg2, 0, W, spec, p->L, pairs, tw, (T)1, st)); }
+            { Timed t_(p, K_MIDDLE_CONV, st); PA_CUDA(launch_middle<T>(s.lg2, 0, W, spec, p->L, pairs, tw, one<T>(), st)); }
         }
         { Timed t_(p, K_INV_BITS, st); PA_CUDA(launch_inv_bits<T>(s.lg1, W, p->L, p->m, nk, popc + k0, marg + k0, op, ostride, pairs, tw, st)); }
     }
@@ -334,7 +395,6 @@ int pa_plan(uint64_t n, uint64_t m, pa_dtype_t dtype, pa_plan_t **out) {
     *out = nullptr;
     if (n == 0 || m == 0 || m > n || n > (1ull << 27)) return PA_EINVAL;
     if (dtype != PA_FP64 && dtype != PA_FP32_GUARD && dtype != PA_NTT64) return PA_EINVAL;
-    if (dtype == PA_NTT64) return PA_EUNSUPPORTED;
     pa_plan_t *p = new pa_plan_t();
     p->n = n;
     p->m = m;
@@ -352,8 +412,10 @@ int pa_plan(uint64_t n, uint64_t m, pa_dtype_t dtype, pa_plan_t **out) {
     }
     p->lgL = lgL;
     p->L = 1ull << lgL;
-    p->shape = choose_shape(lgL, dtype == PA_FP64);
-    int rc = (dtype == PA_FP32_GUARD) ? build_twiddles<float>(p) : build_twiddles<double>(p);
+    p->shape = choose_shape(lgL, dtype);
+    int rc = (dtype == PA_FP32_GUARD) ? build_twiddles<float>(p)
+             : (dtype == PA_FP64)     ? build_twiddles<double>(p)
+                                      : build_twiddles<Zp>(p);
     if (rc != PA_OK) {
         free_plan(p);
         return rc;
@@ -434,7 +496,9 @@ int pa_set_seed(pa_plan_t *p, const uint64_t *seed_dev, uint64_t seed_bits, pa_s
     const size_t sw = (size_t)((seed_bits + 63) / 64);
     if (!p->seed_copy) PA_CUDA(cudaMalloc(&p->seed_copy, sw * sizeof(uint64_t)));
     PA_CUDA(cudaMemcpyAsync(p->seed_copy, seed_dev, sw * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
-    rc = (p->dtype == PA_FP32_GUARD) ? run_seed<float>(p, p->seed_copy, st) : run_seed<double>(p, p->seed_copy, st);
+    rc = (p->dtype == PA_FP32_GUARD) ? run_seed<float>(p, p->seed_copy, st)
+         : (p->dtype == PA_FP64)     ? run_seed<double>(p, p->seed_copy, st)
+                                     : run_seed<Zp>(p, p->seed_copy, st);
     if (rc != PA_OK) return rc;
     p->seeded = true;
     if (p->fallback) p->fallback->seeded = false;  // re-seeded lazily on the next escalation
@@ -458,10 +522,12 @@ int pa_hash_batch(pa_plan_t *p, const uint64_t *keys_dev, uint32_t nkeys, uint64
     if (rc != PA_OK) return rc;
     rc = ensure_keys(p, nkeys);
     if (rc != PA_OK) return rc;
-    rc = (p->dtype == PA_FP32_GUARD)
-             ? run_keys<float>(p, keys_dev, nkeys, key_stride_words, out_dev, out_stride_words, p->popc, p->marg, st)
-             : run_keys<double>(p, keys_dev, nkeys, key_stride_words, out_dev, out_stride_words, p->popc, p->marg,
-                                st);
+    if (p->dtype == PA_FP32_GUARD)
+        rc = run_keys<float>(p, keys_dev, nkeys, key_stride_words, out_dev, out_stride_words, p->popc, p->marg, st);
+    else if (p->dtype == PA_FP64)
+        rc = run_keys<double>(p, keys_dev, nkeys, key_stride_words, out_dev, out_stride_words, p->popc, p->marg, st);
+    else
+        rc = run_keys<Zp>(p, keys_dev, nkeys, key_stride_words, out_dev, out_stride_words, p->popc, p->marg, st);
     if (rc != PA_OK) return rc;
     if (info) info->escalated = 0;
     const bool need_margins = (p->dtype == PA_FP32_GUARD) || info != nullptr;
@@ -475,12 +541,11 @@ int pa_hash_batch(pa_plan_t *p, const uint64_t *keys_dev, uint32_t nkeys, uint64
     for (uint32_t k = 0; k < nkeys; ++k) {
         float mk_ = p->h_marg[k];
         int32_t mode = (int32_t)p->dtype;
-        if (!(mk_ <= p->guard)) {
-            if (p->dtype != PA_FP32_GUARD) return PA_EPRECISION;
-            // Recompute this key in FP64 (the guard's escalation).
+        if (p->dtype != PA_NTT64 && !(mk_ <= p->guard)) {
+            // Recompute this key one mode wider (the guard's escalation): FP32 -> FP64 -> exact NTT.
             if (!p->fallback) {
                 pa_plan_t *fb = nullptr;
-                rc = pa_plan(p->n, p->m, PA_FP64, &fb);
+                rc = pa_plan(p->n, p->m, p->dtype == PA_FP32_GUARD ? PA_FP64 : PA_NTT64, &fb);
                 if (rc != PA_OK) return rc;
                 p->fallback = fb;
             }

@@ -45,6 +45,47 @@ template <> struct Magic<double> { static constexpr double v = 6755399441055744.
 __device__ __forceinline__ uint32_t low_bit(float x) { return __float_as_uint(x) & 1u; }
 __device__ __forceinline__ uint32_t low_bit(double x) { return (uint32_t)__double_as_longlong(x) & 1u; }
 
+// Encoding of inputs and decoding of outputs per arithmetic.
+// Complex: key bits 0/1 in the real (key 2p) and imaginary (key 2p+1) parts,
+// seed as +-1; the decoded value is w = ((P mod 4) - r)/2 (see above).
+// Zp: key 2p + 2^32 * key 2p+1 packed in one residue, seed as 0/1; the
+// convolution counts c_a, c_b < 2^32 come out exactly as the low and high
+// halves of the canonical residue.
+template <typename T> struct Enc {
+    using E = cx<T>;
+    using M = T;  // margin accumulator
+    static __device__ __forceinline__ E key_pair(uint32_t ba, uint32_t bb) {
+        return Arith<T>::mk(ba ? (T)1 : (T)0, bb ? (T)1 : (T)0);
+    }
+    static __device__ __forceinline__ E seed(bool in_range, uint32_t bit) {
+        return Arith<T>::mk(in_range ? (bit ? (T)-1 : (T)1) : (T)0, (T)0);
+    }
+    // bits and margins of the two keys carried by v
+    static __device__ __forceinline__ void decode(E v, uint32_t popa, uint32_t popb, bool valid, bool &bit_a,
+                                                  bool &bit_b, M &ma, M &mb) {
+        const T wa = ((T)(popa & 3u) - v.x) * (T)0.5, wb = ((T)(popb & 3u) - v.y) * (T)0.5;
+        const T fa = wa + Magic<T>::v, fb = wb + Magic<T>::v;  // rint via the 1.5*2^p addition
+        bit_a = valid && low_bit(fa);
+        bit_b = valid && low_bit(fb);
+        if (valid) {
+            // beyond the limit the parity is not resolvable: report a margin of 1 so the guard escalates
+            ma = fmax(ma, fabs(wa) < Magic<T>::limit ? fabs(wa - (fa - Magic<T>::v)) : (T)1);
+            mb = fmax(mb, fabs(wb) < Magic<T>::limit ? fabs(wb - (fb - Magic<T>::v)) : (T)1);
+        }
+    }
+};
+template <> struct Enc<Zp> {
+    using E = cx<Zp>;
+    using M = float;
+    static __device__ __forceinline__ E key_pair(uint32_t ba, uint32_t bb) { return (E)ba | ((E)bb << 32); }
+    static __device__ __forceinline__ E seed(bool in_range, uint32_t bit) { return (in_range && bit) ? 1ull : 0ull; }
+    static __device__ __forceinline__ void decode(E v, uint32_t, uint32_t, bool valid, bool &bit_a, bool &bit_b, M &,
+                                                  M &) {
+        bit_a = valid && (v & 1ull);
+        bit_b = valid && ((v >> 32) & 1ull);
+    }
+};
+
 // ---------------------------------------------------------------------------
 // popcount P of each key (bits < n) and reset of its rounding margin.
 __global__ void k_prep(const uint64_t *__restrict__ keys, uint32_t nkeys, uint64_t kstride, uint64_t n,
@@ -79,7 +120,7 @@ __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
             ba = (uint32_t)(__ldg(ka + a * S64) >> sh) & 1u;
             if (has_b) bb = (uint32_t)(__ldg(kb + a * S64) >> sh) & 1u;
         }
-        v[s] = mk<T>(ba ? (T)1 : (T)0, bb ? (T)1 : (T)0);
+        v[s] = Enc<T>::key_pair(ba, bb);
     }
     cta_fft<T, LEN, COLS, E, false>(sm, v, tq, col, tw);
     cx<T> *w = W + (uint64_t)pair * L;
@@ -106,9 +147,9 @@ __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
         const uint64_t pos = (uint64_t)idx_r0<LEN, E>(tq, s) * S + u;
         uint64_t j = pos + n - 1;  // seed index whose value sits at rotated position pos
         if (j >= L) j -= L;
-        T val = 0;
-        if (j < sbits) val = ((__ldg(seed + (j >> 6)) >> (j & 63)) & 1u) ? (T)-1 : (T)1;
-        v[s] = mk<T>(val, (T)0);
+        const bool in_range = j < sbits;
+        const uint32_t bit = in_range ? (uint32_t)(__ldg(seed + (j >> 6)) >> (j & 63)) & 1u : 0u;
+        v[s] = Enc<T>::seed(in_range, bit);
     }
     cta_fft<T, LEN, COLS, E, false>(sm, v, tq, col, tw);
     twiddle_chain<T, false, E>(v, tw, (uint32_t)(tq * u), (uint32_t)((LEN / E) * u));
@@ -152,7 +193,7 @@ __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
 // only, scaled by 1/L, written as the seed spectrum.
 template <typename T, int LEN, int E, int MODE>
 __global__ void __launch_bounds__(LEN / E)
-    k_middle(cx<T> *__restrict__ W, cx<T> *__restrict__ spec, uint64_t L, TwTab<T> tw, T scale) {
+    k_middle(cx<T> *__restrict__ W, cx<T> *__restrict__ spec, uint64_t L, TwTab<T> tw, cx<T> scale) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T> *sm = reinterpret_cast<cx<T> *>(smem_raw);
     const uint32_t tq = threadIdx.x;
@@ -165,11 +206,11 @@ __global__ void __launch_bounds__(LEN / E)
     cta_fft<T, LEN, 1, E, false>(sm, v, tq, 0, tw);
     if (MODE == 1) {
 #pragma unroll
-        for (int s = 0; s < E; ++s) sp[idx_e<LEN, E>(tq, s)] = cscale<T>(v[s], scale);
+        for (int s = 0; s < E; ++s) sp[idx_e<LEN, E>(tq, s)] = Arith<T>::mul(v[s], scale);
         return;
     }
 #pragma unroll
-    for (int s = 0; s < E; ++s) v[s] = cmul<T>(v[s], sp[idx_e<LEN, E>(tq, s)]);
+    for (int s = 0; s < E; ++s) v[s] = Arith<T>::mul(v[s], sp[idx_e<LEN, E>(tq, s)]);
     __syncthreads();  // the forward transform's last shared-memory reads are done
     cta_fft<T, LEN, 1, E, true>(sm, v, tq, 0, tw);
 #pragma unroll
@@ -213,26 +254,18 @@ __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
     twiddle_chain<T, true, E>(v, tw, (uint32_t)(tq * u), (uint32_t)((LEN / E) * u));
     cta_fft<T, LEN, COLS, E, true>(sm, v, tq, col, tw);
 
-    const T pa4 = (T)(popc[ka] & 3u);
-    const T pb4 = has_b ? (T)(popc[kb] & 3u) : (T)0;
+    const uint32_t popa = popc[ka];
+    const uint32_t popb = has_b ? popc[kb] : 0u;
     word_t *oa = reinterpret_cast<word_t *>(out + (uint64_t)ka * ostride);
     word_t *ob = reinterpret_cast<word_t *>(out + (uint64_t)kb * ostride);
     const uint64_t nchunks = ((m + 63) >> 6) * (64 / COLS);
-    T ma = 0, mb = 0;
+    typename Enc<T>::M ma = 0, mb = 0;
 #pragma unroll
     for (int s = 0; s < E; ++s) {
         const uint64_t t1 = idx_r0<LEN, E>(tq, s);
         const uint64_t i = t1 * S + u;
-        const bool valid = i < m;
-        const T wa = (pa4 - v[s].x) * (T)0.5, wb = (pb4 - v[s].y) * (T)0.5;
-        const T fa = wa + Magic<T>::v, fb = wb + Magic<T>::v;  // rint via the 1.5*2^p addition
-        const bool bit_a = valid && low_bit(fa);
-        const bool bit_b = valid && low_bit(fb);
-        if (valid) {
-            // beyond 2^21 (float) the parity is not resolvable: report a margin of 1 so the guard escalates
-            ma = fmax(ma, fabs(wa) < Magic<T>::limit ? fabs(wa - (fa - Magic<T>::v)) : (T)1);
-            mb = fmax(mb, fabs(wb) < Magic<T>::limit ? fabs(wb - (fb - Magic<T>::v)) : (T)1);
-        }
+        bool bit_a, bit_b;
+        Enc<T>::decode(v[s], popa, popb, i < m, bit_a, bit_b, ma, mb);
         const uint32_t ba = __ballot_sync(0xffffffffu, bit_a);
         const uint32_t bb = __ballot_sync(0xffffffffu, bit_b);
         if (col == 0) {

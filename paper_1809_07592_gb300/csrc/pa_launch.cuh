@@ -86,7 +86,7 @@ cudaError_t launch_mid(int lgLEN, bool inverse, cx<T> *W, uint64_t L, uint32_t l
 
 template <typename T>
 cudaError_t launch_middle(int lgLEN, int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pairs, TwTab<T> tw,
-                          T scale, cudaStream_t st) {
+                          cx<T> scale, cudaStream_t st) {
     constexpr int E = Shape<T>::E;
     return by_len<kMinLgMiddle, MaxLgMiddle<T>::v>(lgLEN, [&](auto c) {
         constexpr int LEN = decltype(c)::value;
@@ -131,7 +131,7 @@ cudaError_t launch_inv_bits(int lgLEN, const cx<T> *W, uint64_t L, uint64_t m, u
                                             TwTab<T>, cudaStream_t);                                             \
     template cudaError_t launch_mid<T>(int, bool, cx<T> *, uint64_t, uint32_t, uint32_t, TwTab<T>,               \
                                        cudaStream_t);                                                           \
-    template cudaError_t launch_middle<T>(int, int, cx<T> *, cx<T> *, uint64_t, uint32_t, TwTab<T>, T,           \
+    template cudaError_t launch_middle<T>(int, int, cx<T> *, cx<T> *, uint64_t, uint32_t, TwTab<T>, cx<T>,       \
                                           cudaStream_t);                                                        \
     template cudaError_t launch_inv_bits<T>(int, const cx<T> *, uint64_t, uint64_t, uint32_t, const uint32_t *,  \
                                             uint32_t *, uint64_t *, uint64_t, uint32_t, TwTab<T>, cudaStream_t);

@@ -19,12 +19,14 @@ namespace pa {
 template <typename T> struct Shape;
 template <> struct Shape<float> { static constexpr int E = 16, COLS = 16; };
 template <> struct Shape<double> { static constexpr int E = 8, COLS = 8; };
+template <> struct Shape<Zp> { static constexpr int E = 8, COLS = 8; };
 
 // Supported pass lengths (log2).
 constexpr int kMinLgStrided = 6, kMaxLgStrided = 10;
 template <typename T> struct MaxLgMiddle;
 template <> struct MaxLgMiddle<float> { static constexpr int v = 14; };
 template <> struct MaxLgMiddle<double> { static constexpr int v = 13; };
+template <> struct MaxLgMiddle<Zp> { static constexpr int v = 13; };
 constexpr int kMinLgMiddle = 6;
 
 cudaError_t launch_prep(const uint64_t *keys, uint32_t nkeys, uint64_t kstride, uint64_t n, uint32_t *popc,
@@ -41,7 +43,7 @@ cudaError_t launch_mid(int lgLEN, bool inverse, cx<T> *W, uint64_t L, uint32_t l
                        cudaStream_t st);
 template <typename T>
 cudaError_t launch_middle(int lgLEN, int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pairs, TwTab<T> tw,
-                          T scale, cudaStream_t st);
+                          cx<T> scale, cudaStream_t st);
 template <typename T>
 cudaError_t launch_inv_bits(int lgLEN, const cx<T> *W, uint64_t L, uint64_t m, uint32_t nkeys,
                             const uint32_t *popc, uint32_t *margin_bits, uint64_t *out, uint64_t ostride,

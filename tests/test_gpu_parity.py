@@ -10,8 +10,8 @@ from tests.gpu_util import sample_rows, to_dev, to_host, unpack_rows
 
 pytestmark = pytest.mark.gpu
 
-MODES = [pa.PA_FP32_GUARD, pa.PA_FP64]
-MODE_ID = {pa.PA_FP32_GUARD: "fp32g", pa.PA_FP64: "fp64"}
+MODES = [pa.PA_FP32_GUARD, pa.PA_FP64, pa.PA_NTT64]
+MODE_ID = {pa.PA_FP32_GUARD: "fp32g", pa.PA_FP64: "fp64", pa.PA_NTT64: "ntt64"}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -85,6 +85,17 @@ def test_tail_bits_ignored_and_output_tail_zero():
         plan.close()
 
 
+def test_fp64_escalates_to_ntt():
+    """FP64 keys that fail the guard are recomputed with the exact transform."""
+    n, m = 20000, 7000
+    seed = inputs.bernoulli_bits(12, 1, n + m - 1)
+    keys = inputs.batch_keys(n, 2, base_seed=12)
+    got, marg, mode, esc, _ = run(n, m, pa.PA_FP64, keys, seed, guard=-1.0)
+    assert esc == 2 and (mode == pa.PA_NTT64).all() and (marg == 0).all()
+    for k in range(2):
+        np.testing.assert_array_equal(got[k], oracle.toeplitz_hash(n, m, seed, keys[k]))
+
+
 def test_forced_escalation_keeps_bits():
     """Guard threshold below every margin: each key goes through the FP64 recomputation."""
     n, m = 30000, 12000
@@ -141,7 +152,7 @@ def test_every_pass_length(dtype):
 @pytest.mark.parametrize("dtype", MODES, ids=MODE_ID.get)
 def test_three_level_plan(dtype):
     """Sizes beyond one CTA's innermost transform use the three-pass split."""
-    lgL = 25 if dtype == pa.PA_FP32_GUARD else 24
+    lgL = 25 if dtype == pa.PA_FP32_GUARD else 24  # FP64 and NTT64 split earlier (wider elements)
     n = (1 << (lgL - 1)) + 1000
     m = (1 << (lgL - 2)) - 3
     key, seed = inputs.block_inputs(n, m, base_seed=77)
