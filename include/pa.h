@@ -147,6 +147,34 @@ int pa_profile_enable(pa_plan_t *plan, int enable);
 /* stats: caller array of PA_NUM_KERNEL_KINDS entries; *count receives the number filled. */
 int pa_profile_read(pa_plan_t *plan, pa_kernel_stat_t *stats, int *count, int reset);
 
+/*
+ * pa_hash_static -- the hash of one or two keys that share one seed, computed
+ * without allocating any memory. The paper has no counterpart to this entry
+ * point: it serves callers that cannot call cudaMalloc, such as a process whose
+ * device memory is wholly reserved by another framework's caching allocator, a
+ * real-time key-distillation loop that must not pay cudaMalloc's latency or
+ * cudaFree's device-wide synchronisation, or an embedding that forbids dynamic
+ * allocation after start-up.
+ *
+ * All scratch (work slot, seed spectrum, twiddle tables, per-key counters) sits
+ * in one static device array of 65 MiB inside libpa.so, which every GPU that
+ * loads the library holds until the process exits. Limits: n + m - 1 <= 2^21
+ * (larger sizes return PA_EUNSUPPORTED), nkeys is 1 or 2. Arguments are those of
+ * pa_plan + pa_set_seed + pa_hash_batch for one call (seed_dev holds n+m-1 bits);
+ * margin, if not NULL, receives the larger rounding margin of the keys (host).
+ *
+ * The first call on a device looks up the array's device address on that device
+ * (cudaGetSymbolAddress); make that first call before any stream capture. Every
+ * call re-transforms the seed and reuses the same array, which keeps the last
+ * call's contents: calls that overlap on the GPU (different streams, or threads)
+ * race and must be serialised by the caller. PA_FP32_GUARD calls, and any call
+ * with margin != NULL, wait for the stream to read the margin back; a key pair
+ * whose margin exceeds 0.25 is recomputed in FP64 (then NTT64) in the same array.
+ */
+int pa_hash_static(uint64_t n, uint64_t m, pa_dtype_t dtype, const uint64_t *seed_dev, const uint64_t *keys_dev,
+                   uint32_t nkeys, uint64_t key_stride_words, uint64_t *out_dev, uint64_t out_stride_words,
+                   pa_stream_t stream, float *margin);
+
 /* Text for an error code; never NULL. */
 const char *pa_strerror(int code);
 

@@ -212,3 +212,21 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def pa_hash_static(n: int, m: int, dtype, seed, keys, nkeys: int, key_stride_words: int, out,
+                   out_stride_words: int, stream=None) -> float:
+    """Allocation-free hash of 1 or 2 keys (see pa_hash_static in pa.h); returns the rounding margin."""
+    L = lib()
+    if getattr(L.pa_hash_static, "_pa_typed", None) is None:
+        u64, u32, vp = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p
+        L.pa_hash_static.argtypes = [u64, u64, ctypes.c_int, vp, vp, u32, u64, vp, u64, vp,
+                                     ctypes.POINTER(ctypes.c_float)]
+        L.pa_hash_static.restype = ctypes.c_int
+        L.pa_hash_static._pa_typed = True
+    if isinstance(dtype, str):
+        dtype = DTYPES[dtype]
+    marg = ctypes.c_float(0.0)
+    _check(L.pa_hash_static(n, m, dtype, _ptr(seed), _ptr(keys), nkeys, key_stride_words, _ptr(out),
+                            out_stride_words, _stream_handle(stream), ctypes.byref(marg)), "pa_hash_static")
+    return marg.value

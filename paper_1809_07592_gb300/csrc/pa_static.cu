@@ -1,0 +1,220 @@
+// pa_static.cu -- pa_hash_static: the hash of one or two keys without any
+// device allocation.
+//
+// Some callers of this library cannot call cudaMalloc: a process whose device
+// memory is entirely reserved by another framework's caching allocator, a
+// real-time key-distillation loop that must not pay cudaMalloc's latency or
+// the device-wide synchronisation of cudaFree, or an embedding that forbids
+// dynamic allocation after start-up. pa_plan allocates its work buffers, so
+// those callers use this entry point instead. All of its scratch -- the
+// transform work slot, the seed spectrum, the twiddle tables and the per-key
+// counters -- lives in one file-scope __device__ array of kScratchBytes bytes
+// (65 MiB), which every GPU that loads the library holds until the process
+// exits. Inputs and outputs stay caller-owned.
+//
+// The paper has no counterpart to this entry point; it is a deployment aid.
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <type_traits>
+
+#include "pa.h"
+#include "pa_launch.h"
+
+using namespace pa;
+
+namespace {
+
+// Largest supported transform: complex length 2^21 (n + m - 1 <= 2^21, e.g. the
+// n = 2^20, m <= n/2 blocks), two slots (work + spectrum) of FP64 complex values,
+// plus twiddle tables and per-key counters.
+constexpr int kMaxLgL = 21;
+constexpr size_t kSlotBytes = ((size_t)1 << kMaxLgL) * 16;        // 32 MiB
+constexpr size_t kScratchBytes = 2 * kSlotBytes + ((size_t)1 << 20);  // + 1 MiB tables and counters
+
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+unsigned char *g_scratch_addr[kMaxDevices] = {};  // device address of g_scratch, per device
+
+// Device address of g_scratch on the current device, looked up once per device.
+int scratch_address(unsigned char **out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PA_ECUDA;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_scratch_addr[dev]) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_scratch) != cudaSuccess || !ptr) return PA_ECUDA;
+        g_scratch_addr[dev] = static_cast<unsigned char *>(ptr);
+    }
+    *out = g_scratch_addr[dev];
+    return PA_OK;
+}
+
+// w_L^e for the complex transforms: exp(-2 pi i e / L) in double precision.
+template <typename T>
+__global__ void k_twiddles_complex(cx<T> *hi, cx<T> *lo, uint32_t B, uint32_t lgL) {
+    const uint32_t nhi = 1u << (lgL - B), nlo = 1u << B;
+    const double inv = 1.0 / (double)(1ull << lgL);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nhi + nlo; i += gridDim.x * blockDim.x) {
+        const uint64_t e = i < nhi ? ((uint64_t)i << B) : (uint64_t)(i - nhi);
+        double s, c;
+        sincospi(2.0 * (double)e * inv, &s, &c);
+        cx<T> w;
+        w.x = (T)c;
+        w.y = (T)-s;
+        if (i < nhi) hi[i] = w; else lo[i - nhi] = w;
+    }
+}
+
+// w_L^e modulo p for the exact transform, by square-and-multiply from the root w.
+__global__ void k_twiddles_zp(uint64_t *hi, uint64_t *lo, uint32_t B, uint32_t lgL, uint64_t w) {
+    const uint32_t nhi = 1u << (lgL - B), nlo = 1u << B;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nhi + nlo; i += gridDim.x * blockDim.x) {
+        uint64_t e = i < nhi ? ((uint64_t)i << B) : (uint64_t)(i - nhi);
+        uint64_t r = 1, b = w;
+        while (e) {
+            if (e & 1) r = zp_mul(r, b);
+            b = zp_mul(b, b);
+            e >>= 1;
+        }
+        if (i < nhi) hi[i] = r; else lo[i - nhi] = r;
+    }
+}
+
+uint64_t mulmod_host(uint64_t a, uint64_t b) {
+    unsigned __int128 x = (unsigned __int128)a * b;
+    return zp_reduce((uint64_t)(x >> 64), (uint64_t)x);
+}
+uint64_t powmod_host(uint64_t a, uint64_t e) {
+    uint64_t r = 1;
+    while (e) {
+        if (e & 1) r = mulmod_host(r, a);
+        a = mulmod_host(a, a);
+        e >>= 1;
+    }
+    return r;
+}
+// Root of order L whose L/32-th power is 2^6 (the in-register root), as in the plans.
+uint64_t root_of_order(uint64_t L) {
+    const uint64_t w = powmod_host(7, (kP - 1) / L);
+    const uint64_t w32 = powmod_host(w, L / 32);
+    for (uint64_t j = 1; j < 64; j += 2)
+        if (powmod_host(w32, j) == 64ull) return powmod_host(w, j);
+    return 0;
+}
+
+template <typename T> cx<T> scale_of(uint64_t L);
+template <> cx<float> scale_of<float>(uint64_t L) { return make_float2((float)(1.0 / (double)L), 0.f); }
+template <> cx<double> scale_of<double>(uint64_t L) { return make_double2(1.0 / (double)L, 0.0); }
+template <> cx<Zp> scale_of<Zp>(uint64_t L) { return powmod_host(L, kP - 2); }
+template <typename T> cx<T> unit();
+template <> cx<float> unit<float>() { return make_float2(1.f, 0.f); }
+template <> cx<double> unit<double>() { return make_double2(1.0, 0.0); }
+template <> cx<Zp> unit<Zp>() { return 1ull; }
+
+#define STATIC_CUDA(x)                               \
+    do {                                             \
+        if ((x) != cudaSuccess) return PA_ECUDA;     \
+    } while (0)
+
+// One complete hash of nkeys (1 or 2) keys, every buffer carved from g_scratch.
+template <typename T>
+int run_static(unsigned char *base, int lgL, uint64_t n, uint64_t m, const uint64_t *seed, const uint64_t *keys,
+               uint32_t nkeys, uint64_t kstride, uint64_t *out, uint64_t ostride, cudaStream_t st) {
+    const uint64_t L = 1ull << lgL;
+    cx<T> *W = reinterpret_cast<cx<T> *>(base);
+    cx<T> *spec = reinterpret_cast<cx<T> *>(base + kSlotBytes);
+    unsigned char *tail = base + 2 * kSlotBytes;
+    const uint32_t B = (uint32_t)(lgL + 1) / 2;
+    cx<T> *hi = reinterpret_cast<cx<T> *>(tail);
+    cx<T> *lo = hi + (1u << (lgL - B));
+    uint32_t *popc = reinterpret_cast<uint32_t *>(tail + (512u << 10));
+    uint32_t *marg = popc + 2;
+    if constexpr (std::is_same<T, Zp>::value) {
+        const uint64_t w = root_of_order(L);
+        if (!w) return PA_EUNSUPPORTED;
+        k_twiddles_zp<<<64, 256, 0, st>>>(reinterpret_cast<uint64_t *>(hi), reinterpret_cast<uint64_t *>(lo), B,
+                                          (uint32_t)lgL, w);
+    } else {
+        k_twiddles_complex<T><<<64, 256, 0, st>>>(hi, lo, B, (uint32_t)lgL);
+    }
+    STATIC_CUDA(cudaGetLastError());
+    TwTab<T> tw;
+    tw.hi = hi;
+    tw.lo = lo;
+    tw.B = B;
+    tw.lgL = (uint32_t)lgL;
+    int lg1 = lgL - 12;
+    if (lg1 < kMinLgStrided) lg1 = kMinLgStrided;
+    if (lg1 > kMaxLgStrided) lg1 = kMaxLgStrided;
+    const int lg2 = lgL - lg1;  // <= 12 for lgL <= 21: always a two-level split
+    STATIC_CUDA(launch_fwd_seed<T>(lg1, seed, n, m, W, L, tw, st));
+    STATIC_CUDA(launch_middle<T>(lg2, 1, W, spec, L, 1, tw, scale_of<T>(L), st));
+    STATIC_CUDA(launch_prep(keys, nkeys, kstride, n, popc, marg, st));  // also zeroes the margins
+    STATIC_CUDA(launch_fwd_keys<T>(lg1, keys, nkeys, kstride, n, W, L, 1, tw, st));
+    STATIC_CUDA(launch_middle<T>(lg2, 0, W, spec, L, 1, tw, unit<T>(), st));
+    STATIC_CUDA(launch_inv_bits<T>(lg1, W, L, m, nkeys, popc, marg, out, ostride, 1, tw, st));
+    return PA_OK;
+}
+
+}  // namespace
+
+extern "C" int pa_hash_static(uint64_t n, uint64_t m, pa_dtype_t dtype, const uint64_t *seed_dev,
+                              const uint64_t *keys_dev, uint32_t nkeys, uint64_t key_stride_words,
+                              uint64_t *out_dev, uint64_t out_stride_words, pa_stream_t stream, float *margin) {
+    if (n == 0 || m == 0 || m > n || !seed_dev || !keys_dev || !out_dev) return PA_EINVAL;
+    if (nkeys < 1 || nkeys > 2) return PA_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(seed_dev) | reinterpret_cast<uintptr_t>(keys_dev) |
+         reinterpret_cast<uintptr_t>(out_dev)) & 15u)
+        return PA_EINVAL;
+    if (key_stride_words < (n + 63) / 64 || out_stride_words < (m + 63) / 64) return PA_EINVAL;
+    if (nkeys == 2 && ((key_stride_words | out_stride_words) & 1)) return PA_EINVAL;
+    if (dtype != PA_FP32_GUARD && dtype != PA_FP64 && dtype != PA_NTT64) return PA_EINVAL;
+    int lgL = 12;
+    while ((1ull << lgL) < n + m - 1) ++lgL;
+    if (lgL > kMaxLgL) return PA_EUNSUPPORTED;  // beyond the static scratch: n + m - 1 must be <= 2^21
+
+    unsigned char *base = nullptr;
+    int rc = scratch_address(&base);
+    if (rc != PA_OK) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    uint32_t *marg = reinterpret_cast<uint32_t *>(base + 2 * kSlotBytes + (512u << 10)) + 2;
+
+    if (dtype == PA_NTT64) {
+        rc = run_static<Zp>(base, lgL, n, m, seed_dev, keys_dev, nkeys, key_stride_words, out_dev,
+                            out_stride_words, st);
+        if (rc == PA_OK && margin) margin[0] = 0.f;
+        return rc;
+    }
+    pa_dtype_t mode = dtype;
+    for (;;) {
+        rc = (mode == PA_FP32_GUARD) ? run_static<float>(base, lgL, n, m, seed_dev, keys_dev, nkeys, key_stride_words,
+                                                        out_dev, out_stride_words, st)
+                                     : run_static<double>(base, lgL, n, m, seed_dev, keys_dev, nkeys,
+                                                          key_stride_words, out_dev, out_stride_words, st);
+        if (rc != PA_OK) return rc;
+        if (mode == PA_FP64 && !margin) return PA_OK;  // FP64 needs no readback unless asked
+        uint32_t mb[2] = {0u, 0u};  // caller's stack, pageable: no allocation
+        STATIC_CUDA(cudaMemcpyAsync(mb, marg, nkeys * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        STATIC_CUDA(cudaStreamSynchronize(st));
+        float worst = 0.f;
+        for (uint32_t k = 0; k < nkeys; ++k) {
+            float f;
+            memcpy(&f, &mb[k], sizeof(f));
+            if (f > worst) worst = f;
+        }
+        if (worst <= 0.25f) {
+            if (margin) margin[0] = worst;
+            return PA_OK;
+        }
+        if (mode == PA_FP64) {  // FP64 failed its guard: recompute exactly
+            rc = run_static<Zp>(base, lgL, n, m, seed_dev, keys_dev, nkeys, key_stride_words, out_dev,
+                                out_stride_words, st);
+            if (rc == PA_OK && margin) margin[0] = 0.f;
+            return rc;
+        }
+        mode = PA_FP64;  // FP32 failed its guard: recompute in FP64 in the same scratch
+    }
+}
