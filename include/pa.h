@@ -129,6 +129,69 @@ int pa_plan_set_guard(pa_plan_t *plan, float threshold);
 /* Plan introspection (no GPU work): transform length L and pass lengths L1, L2, L3 (L3 = 1 for two passes). */
 int pa_plan_shape(const pa_plan_t *plan, uint64_t *L, uint32_t *L1, uint32_t *L2, uint32_t *L3);
 
+/* ---------------------------------------------------------------------------------------
+ * Uneven batch: blocks of different (n, m), each with its own key and seed, as reconciliation
+ * emits them.
+ * ------------------------------------------------------------------------------------- */
+
+/* One privacy-amplification block. All pointers are device pointers, 16-byte aligned:
+ * key ceil(n/64) words, seed ceil((n+m-1)/64) words, out ceil(m/64) words. */
+typedef struct {
+    uint64_t n, m;
+    const uint64_t *key;
+    const uint64_t *seed;
+    uint64_t *out;
+} pa_block_desc_t;
+
+typedef struct pa_uneven pa_uneven_t;
+
+/*
+ * pa_uneven_create -- plan an uneven batch. Blocks are grouped by transform length
+ * L = 2^ceil(log2(n+m-1)) (at least 2^12); every class gets its own work buffers, twiddle
+ * tables and a device copy of its block descriptors, and its pass split is chosen by the
+ * built-in autotuner (timed on the class's own buffers, cached per (L, dtype) for the process
+ * and, if the environment variable PA_TUNE_CACHE names a file, across processes).
+ * In PA_FP32_GUARD and PA_FP64 mode each block's key and seed share one complex transform,
+ * z = x + i*sigma, and are separated after the forward transform with the paper's real-valued
+ * FFT identities (Eq. 5-10); two blocks share each inverse transform. PA_NTT64 blocks run one
+ * exact transform chain each. With use_graph != 0 all launches are captured once into a CUDA
+ * graph (one branch per length class, the classes run concurrently) and pa_uneven_run replays it.
+ *   blocks   caller array of nblocks descriptors (copied; the device buffers they name must
+ *            stay valid until the batch is destroyed or updated)
+ * Returns PA_EINVAL (bad sizes, alignment, nblocks == 0), PA_ENOMEM, PA_EUNSUPPORTED, PA_ECUDA.
+ */
+int pa_uneven_create(const pa_block_desc_t *blocks, uint32_t nblocks, pa_dtype_t dtype, int use_graph,
+                     pa_uneven_t **out);
+
+/*
+ * pa_uneven_update -- point the batch at new key/seed/output buffers. Block i must keep the
+ * (n, m) it was created with (PA_EINVAL otherwise). Stream-ordered on `stream`.
+ */
+int pa_uneven_update(pa_uneven_t *batch, const pa_block_desc_t *blocks, uint32_t nblocks, pa_stream_t stream);
+
+/*
+ * pa_uneven_run -- hash every block (graph replay or direct launches on `stream`). In
+ * PA_FP32_GUARD mode, or when info != NULL, waits for the per-block margins and recomputes
+ * blocks over the 0.25 guard in FP64 (then NTT64); info->margin / info->mode are indexed by
+ * block.
+ */
+int pa_uneven_run(pa_uneven_t *batch, pa_stream_t stream, pa_batch_info_t *info);
+
+/* Rounding-margin threshold of the batch's guard (default 0.25); see pa_plan_set_guard. */
+int pa_uneven_set_guard(pa_uneven_t *batch, float threshold);
+
+/* Release the batch and its device memory (synchronizes the device). NULL is accepted. */
+int pa_uneven_destroy(pa_uneven_t *batch);
+
+/* Describe the split chosen for one length class: returns the number of classes in *nclasses
+ * and, for class c < nclasses, its L, pass lengths and number of blocks. */
+int pa_uneven_class(const pa_uneven_t *batch, uint32_t c, uint32_t *nclasses, uint64_t *L, uint32_t *L1,
+                    uint32_t *L2, uint32_t *L3, uint32_t *nblocks);
+
+/* One-shot convenience: create (without a graph), run, destroy. */
+int pa_hash_uneven(const pa_block_desc_t *blocks, uint32_t nblocks, pa_dtype_t dtype, pa_stream_t stream,
+                   pa_batch_info_t *info);
+
 /*
  * Kernel timing (measurement support, no counterpart in the paper). When enabled,
  * every kernel launch of the plan is bracketed by CUDA events recorded on the

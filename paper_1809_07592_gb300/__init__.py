@@ -50,6 +50,11 @@ class BatchInfo(ctypes.Structure):
                 ("escalated", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
+class BlockDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("m", ctypes.c_uint64), ("key", ctypes.c_void_p), ("seed", ctypes.c_void_p),
+                ("out", ctypes.c_void_p)]
+
+
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
 
@@ -80,12 +85,22 @@ def lib():
                                 ctypes.POINTER(u32)]
     L.pa_profile_enable.argtypes = [vp, ctypes.c_int]
     L.pa_profile_read.argtypes = [vp, ctypes.POINTER(KernelStat), ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+    bdp = ctypes.POINTER(BlockDesc)
+    L.pa_uneven_create.argtypes = [bdp, u32, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]
+    L.pa_uneven_update.argtypes = [vp, bdp, u32, vp]
+    L.pa_uneven_run.argtypes = [vp, vp, ctypes.POINTER(BatchInfo)]
+    L.pa_uneven_set_guard.argtypes = [vp, ctypes.c_float]
+    L.pa_uneven_destroy.argtypes = [vp]
+    L.pa_uneven_class.argtypes = [vp, u32, ctypes.POINTER(u32), ctypes.POINTER(u64), ctypes.POINTER(u32),
+                                  ctypes.POINTER(u32), ctypes.POINTER(u32), ctypes.POINTER(u32)]
+    L.pa_hash_uneven.argtypes = [bdp, u32, ctypes.c_int, vp, ctypes.POINTER(BatchInfo)]
     L.pa_strerror.argtypes = [ctypes.c_int]
     L.pa_strerror.restype = ctypes.c_char_p
     L.pa_last_cuda_error.argtypes = []
     L.pa_last_cuda_error.restype = ctypes.c_char_p
     for name in ("pa_plan", "pa_plan_destroy", "pa_set_seed", "pa_hash_batch", "pa_plan_set_guard",
-                 "pa_plan_shape", "pa_profile_enable", "pa_profile_read"):
+                 "pa_plan_shape", "pa_profile_enable", "pa_profile_read", "pa_uneven_create", "pa_uneven_update",
+                 "pa_uneven_run", "pa_uneven_set_guard", "pa_uneven_destroy", "pa_uneven_class", "pa_hash_uneven"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -169,6 +184,80 @@ def pa_profile_read(plan: int, reset: bool = False) -> dict:
     cnt = ctypes.c_int()
     _check(lib().pa_profile_read(plan, arr, ctypes.byref(cnt), 1 if reset else 0), "pa_profile_read")
     return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms) for i in range(cnt.value)}
+
+
+def _descs(blocks):
+    """blocks: iterable of (n, m, key_tensor, seed_tensor, out_tensor) -> ctypes array of BlockDesc."""
+    blocks = list(blocks)
+    arr = (BlockDesc * len(blocks))()
+    for i, (n, m, k, sd, o) in enumerate(blocks):
+        arr[i] = BlockDesc(n, m, _ptr(k), _ptr(sd), _ptr(o))
+    return arr, len(blocks)
+
+
+def _info_struct(nblocks):
+    marg = (ctypes.c_float * nblocks)()
+    mode = (ctypes.c_int32 * nblocks)()
+    bi = BatchInfo(ctypes.cast(marg, ctypes.POINTER(ctypes.c_float)), ctypes.cast(mode, ctypes.POINTER(ctypes.c_int32)),
+                   0, 0)
+    return bi, marg, mode
+
+
+def pa_uneven_create(blocks, dtype=PA_FP32_GUARD, use_graph: bool = True) -> int:
+    if isinstance(dtype, str):
+        dtype = DTYPES[dtype]
+    arr, nb = _descs(blocks)
+    h = ctypes.c_void_p()
+    _check(lib().pa_uneven_create(arr, nb, dtype, 1 if use_graph else 0, ctypes.byref(h)), "pa_uneven_create")
+    return h.value
+
+
+def pa_uneven_update(batch: int, blocks, stream=None) -> None:
+    arr, nb = _descs(blocks)
+    _check(lib().pa_uneven_update(batch, arr, nb, _stream_handle(stream)), "pa_uneven_update")
+
+
+def pa_uneven_run(batch: int, nblocks: int, stream=None, info: bool = False):
+    if info:
+        bi, marg, mode = _info_struct(nblocks)
+        _check(lib().pa_uneven_run(batch, _stream_handle(stream), ctypes.byref(bi)), "pa_uneven_run")
+        return list(marg), list(mode), bi.escalated
+    _check(lib().pa_uneven_run(batch, _stream_handle(stream), None), "pa_uneven_run")
+    return None
+
+
+def pa_uneven_set_guard(batch: int, threshold: float) -> None:
+    _check(lib().pa_uneven_set_guard(batch, threshold), "pa_uneven_set_guard")
+
+
+def pa_uneven_destroy(batch: int) -> None:
+    _check(lib().pa_uneven_destroy(batch), "pa_uneven_destroy")
+
+
+def pa_uneven_classes(batch: int):
+    """[(L, L1, L2, L3, nblocks)] for every length class of the batch."""
+    nc = ctypes.c_uint32()
+    _check(lib().pa_uneven_class(batch, 0xFFFFFFFF, ctypes.byref(nc), None, None, None, None, None), "pa_uneven_class")
+    out = []
+    for c in range(nc.value):
+        L = ctypes.c_uint64()
+        a, b, d, nb = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+        _check(lib().pa_uneven_class(batch, c, None, ctypes.byref(L), ctypes.byref(a), ctypes.byref(b), ctypes.byref(d),
+                                     ctypes.byref(nb)), "pa_uneven_class")
+        out.append((L.value, a.value, b.value, d.value, nb.value))
+    return out
+
+
+def pa_hash_uneven(blocks, dtype=PA_FP32_GUARD, stream=None, info: bool = False):
+    if isinstance(dtype, str):
+        dtype = DTYPES[dtype]
+    arr, nb = _descs(blocks)
+    if info:
+        bi, marg, mode = _info_struct(nb)
+        _check(lib().pa_hash_uneven(arr, nb, dtype, _stream_handle(stream), ctypes.byref(bi)), "pa_hash_uneven")
+        return list(marg), list(mode), bi.escalated
+    _check(lib().pa_hash_uneven(arr, nb, dtype, _stream_handle(stream), None), "pa_hash_uneven")
+    return None
 
 
 class Plan:

@@ -14,17 +14,23 @@
 
 #include "pa.h"
 #include "pa_launch.h"
+#include "pa_internal.h"
 
 using namespace pa;
 
 namespace {
-
 thread_local std::string g_last_cuda_error;
+}
 
-int cuda_fail(cudaError_t e, const char *what) {
+// Shared with the other translation units of the library (not part of the C ABI).
+int pa_internal_cuda_fail(cudaError_t e, const char *what) {
     g_last_cuda_error = std::string(what) + ": " + cudaGetErrorString(e);
     return PA_ECUDA;
 }
+
+namespace {
+
+int cuda_fail(cudaError_t e, const char *what) { return pa_internal_cuda_fail(e, what); }
 
 #define PA_CUDA(call)                                   \
     do {                                                \
@@ -185,12 +191,11 @@ uint64_t zp_root(uint64_t L) {
 }
 
 template <typename T>
-int build_twiddles(pa_plan_t *p) {
-    const int lgL = p->lgL;
+int make_twiddles(int lgL, void **dhi, void **dlo, uint32_t *Bout) {
     const uint32_t B = (uint32_t)(lgL + 1) / 2;
     const uint64_t nhi = 1ull << (lgL - B), nlo = 1ull << B;
     std::vector<cx<T>> hi(nhi), lo(nlo);
-    const double L = (double)p->L;
+    const double L = (double)(1ull << lgL);
     const double two_pi = 6.283185307179586476925286766559;
     for (uint64_t h = 0; h < nhi; ++h) {
         const double a = two_pi * (double)(h << B) / L;
@@ -202,33 +207,37 @@ int build_twiddles(pa_plan_t *p) {
         lo[l].x = (T)std::cos(a);
         lo[l].y = (T)-std::sin(a);
     }
-    PA_CUDA(cudaMalloc(&p->tw_hi, nhi * sizeof(cx<T>)));
-    PA_CUDA(cudaMalloc(&p->tw_lo, nlo * sizeof(cx<T>)));
-    PA_CUDA(cudaMemcpy(p->tw_hi, hi.data(), nhi * sizeof(cx<T>), cudaMemcpyHostToDevice));
-    PA_CUDA(cudaMemcpy(p->tw_lo, lo.data(), nlo * sizeof(cx<T>), cudaMemcpyHostToDevice));
-    p->twB = B;
+    PA_CUDA(cudaMalloc(dhi, nhi * sizeof(cx<T>)));
+    PA_CUDA(cudaMalloc(dlo, nlo * sizeof(cx<T>)));
+    PA_CUDA(cudaMemcpy(*dhi, hi.data(), nhi * sizeof(cx<T>), cudaMemcpyHostToDevice));
+    PA_CUDA(cudaMemcpy(*dlo, lo.data(), nlo * sizeof(cx<T>), cudaMemcpyHostToDevice));
+    *Bout = B;
     return PA_OK;
 }
 
 template <>
-int build_twiddles<Zp>(pa_plan_t *p) {
-    const int lgL = p->lgL;
+int make_twiddles<Zp>(int lgL, void **dhi, void **dlo, uint32_t *Bout) {
     const uint32_t B = (uint32_t)(lgL + 1) / 2;
     const uint64_t nhi = 1ull << (lgL - B), nlo = 1ull << B;
     std::vector<uint64_t> hi(nhi), lo(nlo);
-    const uint64_t w = zp_root(p->L);
+    const uint64_t w = zp_root(1ull << lgL);
     if (w == 0) return PA_EUNSUPPORTED;
     const uint64_t wB = zp_pow_host(w, 1ull << B);
     uint64_t x = 1;
     for (uint64_t h = 0; h < nhi; ++h) { hi[h] = x; x = zp_mul_host(x, wB); }
     x = 1;
     for (uint64_t l = 0; l < nlo; ++l) { lo[l] = x; x = zp_mul_host(x, w); }
-    PA_CUDA(cudaMalloc(&p->tw_hi, nhi * sizeof(uint64_t)));
-    PA_CUDA(cudaMalloc(&p->tw_lo, nlo * sizeof(uint64_t)));
-    PA_CUDA(cudaMemcpy(p->tw_hi, hi.data(), nhi * sizeof(uint64_t), cudaMemcpyHostToDevice));
-    PA_CUDA(cudaMemcpy(p->tw_lo, lo.data(), nlo * sizeof(uint64_t), cudaMemcpyHostToDevice));
-    p->twB = B;
+    PA_CUDA(cudaMalloc(dhi, nhi * sizeof(uint64_t)));
+    PA_CUDA(cudaMalloc(dlo, nlo * sizeof(uint64_t)));
+    PA_CUDA(cudaMemcpy(*dhi, hi.data(), nhi * sizeof(uint64_t), cudaMemcpyHostToDevice));
+    PA_CUDA(cudaMemcpy(*dlo, lo.data(), nlo * sizeof(uint64_t), cudaMemcpyHostToDevice));
+    *Bout = B;
     return PA_OK;
+}
+
+template <typename T>
+int build_twiddles(pa_plan_t *p) {
+    return make_twiddles<T>(p->lgL, &p->tw_hi, &p->tw_lo, &p->twB);
 }
 
 // 1/L as the element type's scaling factor.
@@ -369,6 +378,12 @@ void free_plan(pa_plan_t *p) {
 }
 
 }  // namespace
+
+int pa_internal_twiddles(int lgL, int dtype, void **hi, void **lo, uint32_t *B) {
+    return dtype == PA_FP32_GUARD ? make_twiddles<float>(lgL, hi, lo, B)
+           : dtype == PA_FP64     ? make_twiddles<double>(lgL, hi, lo, B)
+                                  : make_twiddles<Zp>(lgL, hi, lo, B);
+}
 
 extern "C" {
 

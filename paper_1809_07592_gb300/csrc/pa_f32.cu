@@ -3,4 +3,5 @@
 
 namespace pa {
 PA_INSTANTIATE_LAUNCHERS(float)
+PA_INSTANTIATE_UNEVEN(float)
 }  // namespace pa

@@ -3,4 +3,5 @@
 
 namespace pa {
 PA_INSTANTIATE_LAUNCHERS(double)
+PA_INSTANTIATE_UNEVEN(double)
 }  // namespace pa

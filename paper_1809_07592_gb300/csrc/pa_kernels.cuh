@@ -288,3 +288,188 @@ __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
 }
 
 }  // namespace pa
+
+// ===========================================================================
+// Uneven batch: blocks of different (n, m), each with its own seed, grouped by
+// transform length L. Per block the paper's real-valued FFT acceleration
+// (Eq. 5-10) carries key and seed in one complex transform, z = x + i*sigma;
+// the fused middle pass separates X and V from Z(k) and Z(-k), forms X*V and
+// sends two blocks' products through one inverse transform as Y1 + i*Y2.
+// ===========================================================================
+namespace pa {
+
+// Device-side block descriptor.
+struct BlockDev {
+    uint64_t n, m;
+    const uint64_t *key;   // ceil(n/64) words
+    const uint64_t *seed;  // ceil((n+m-1)/64) words
+    uint64_t *out;         // ceil(m/64) words
+    uint32_t id;           // index of the block in the caller's list (popcount / margin slot)
+    uint32_t pad;
+};
+
+// popcount of each block's key and margin reset (one CTA per block of the class).
+__global__ void k_prep_blocks(const BlockDev *__restrict__ blocks, uint32_t *__restrict__ popc,
+                              uint32_t *__restrict__ margin_bits);
+
+// Level-1 forward pass of z = x + i*sigma for every block of a class. Grid (S/COLS, blocks).
+template <typename T, int LEN, int COLS, int E>
+__global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
+    k_fwd_keyseed(const BlockDev *__restrict__ blocks, cx<T> *__restrict__ W, uint64_t L, TwTab<T> tw) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T> *sm = reinterpret_cast<cx<T> *>(smem_raw);
+    const uint32_t col = threadIdx.x % COLS, tq = threadIdx.x / COLS;
+    const uint64_t S = L >> ilog2(LEN);
+    const uint64_t u = (uint64_t)blockIdx.x * COLS + col;
+    const BlockDev bd = blocks[blockIdx.y];
+    const uint64_t n = bd.n, sbits = bd.n + bd.m - 1;
+    const uint64_t S64 = S >> 6;
+    const uint32_t sh = (uint32_t)(u & 63);
+    const uint64_t *kp = bd.key + (u >> 6);
+    const uint64_t arows = n > u ? (n - u + S - 1) / S : 0;
+    cx<T> v[E];
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+        const uint32_t a = idx_r0<LEN, E>(tq, s);
+        const uint32_t bx = (a < arows) ? (uint32_t)(__ldg(kp + a * S64) >> sh) & 1u : 0u;
+        uint64_t j = (uint64_t)a * S + u + n - 1;  // seed index at rotated position a*S + u
+        if (j >= L) j -= L;
+        const bool in_range = j < sbits;
+        const uint32_t bs = in_range ? (uint32_t)(__ldg(bd.seed + (j >> 6)) >> (j & 63)) & 1u : 0u;
+        v[s] = Arith<T>::mk(bx ? (T)1 : (T)0, in_range ? (bs ? (T)-1 : (T)1) : (T)0);
+    }
+    cta_fft<T, LEN, COLS, E, false>(sm, v, tq, col, tw);
+    cx<T> *w = W + (uint64_t)blockIdx.y * L;
+    twiddle_chain<T, false, E>(v, tw, (uint32_t)(tq * u), (uint32_t)((LEN / E) * u));
+#pragma unroll
+    for (int s = 0; s < E; ++s) w[(uint64_t)idx_e<LEN, E>(tq, s) * S + u] = v[s];
+}
+
+// Storage row of the frequency low part rho (lgM = log2 of the middle strided
+// pass length, 0 for two-level plans): rho = k1 + L1*k2 sits at row k1*M + k2.
+__device__ __forceinline__ uint32_t split_row(uint32_t rho, uint32_t lgL1, uint32_t lgM) {
+    return ((rho & ((1u << lgL1) - 1u)) << lgM) + (rho >> lgL1);
+}
+
+// Fused innermost pass of the uneven batch. CTA (rho, pair): rows rho and
+// -rho of blocks 2*pair and 2*pair+1 (if present), one thread group per row.
+// Forward transform, Eq. 5-10 split with the mirror bin, X*V/L, then the
+// inverse transform of Y1 + i*Y2 written to the pair's slot in Wi.
+template <typename T, int LEN, int E>
+__global__ void __launch_bounds__(2 * (LEN / E))
+    k_middle_split(const cx<T> *__restrict__ Wf, cx<T> *__restrict__ Wi, uint64_t L, uint32_t nblocks,
+                   uint32_t lgL1, uint32_t lgM, TwTab<T> tw, T inv_L) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T> *smem = reinterpret_cast<cx<T> *>(smem_raw);
+    constexpr uint32_t TC = LEN / E;
+    constexpr uint32_t SE = smem_elems<LEN, 1>();
+    const uint32_t g = threadIdx.x / TC, tq = threadIdx.x % TC;
+    const uint32_t R = (uint32_t)(L / LEN);  // rows per block
+    const uint32_t rho = blockIdx.x;          // 0 .. R/2
+    const uint32_t rho_m = (R - rho) & (R - 1);
+    const uint32_t my_rho = g ? rho_m : rho;
+    const uint32_t row = split_row(my_rho, lgL1, lgM);
+    const bool self_paired = rho == rho_m;
+    cx<T> *sm = smem + g * SE;                          // this group's transform scratch
+    const cx<T> *sm_other = smem + (self_paired ? g : 1u - g) * SE;  // where the mirror row's spectrum sits
+    const uint32_t b1 = 2 * blockIdx.y, b2 = b1 + 1;
+    const bool has2 = b2 < nblocks;
+    cx<T> y[E];
+#pragma unroll
+    for (int s = 0; s < E; ++s) y[s] = Arith<T>::mk((T)0, (T)0);
+    for (int which = 0; which < (has2 ? 2 : 1); ++which) {
+        const cx<T> *w = Wf + (uint64_t)(which ? b2 : b1) * L + (uint64_t)row * LEN;
+        cx<T> v[E];
+#pragma unroll
+        for (int s = 0; s < E; ++s) v[s] = w[idx_r0<LEN, E>(tq, s)];
+        __syncthreads();  // previous use of the scratch is finished
+        cta_fft<T, LEN, 1, E, false>(sm, v, tq, 0, tw);
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < E; ++s) sm[sidx<1>(idx_e<LEN, E>(tq, s), 0)] = v[s];
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < E; ++s) {
+            const uint32_t p = idx_e<LEN, E>(tq, s);
+            const uint32_t pm = (my_rho == 0) ? ((LEN - p) & (LEN - 1)) : (LEN - 1 - p);
+            const cx<T> z = v[s], zm = sm_other[sidx<1>(pm, 0)];
+            // Eq. 7-10: X = (Z(k) + conj Z(-k)) / 2, V = (Z(k) - conj Z(-k)) / (2i)
+            const cx<T> X = Arith<T>::mk((z.x + zm.x) * (T)0.5, (z.y - zm.y) * (T)0.5);
+            const cx<T> V = Arith<T>::mk((z.y + zm.y) * (T)0.5, (zm.x - z.x) * (T)0.5);
+            cx<T> Y = Arith<T>::mul(X, V);
+            Y.x *= inv_L;
+            Y.y *= inv_L;
+            if (which == 0) {
+                y[s] = Y;
+            } else {  // y += i * Y2
+                y[s].x -= Y.y;
+                y[s].y += Y.x;
+            }
+        }
+    }
+    __syncthreads();
+    cta_fft<T, LEN, 1, E, true>(sm, y, tq, 0, tw);
+    if (self_paired && g == 1) return;
+    cx<T> *wo = Wi + (uint64_t)blockIdx.y * L + (uint64_t)row * LEN;
+#pragma unroll
+    for (int s = 0; s < E; ++s) wo[idx_r0<LEN, E>(tq, s)] = y[s];
+}
+
+// Level-1 inverse pass with bit output for pairs of blocks (real part: block
+// 2p, imaginary part: block 2p+1), each with its own m and output pointer.
+template <typename T, int LEN, int COLS, int E>
+__global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
+    k_inv_bits_blocks(const cx<T> *__restrict__ W, uint64_t L, const BlockDev *__restrict__ blocks, uint32_t nblocks,
+                      const uint32_t *__restrict__ popc, uint32_t *__restrict__ margin_bits, TwTab<T> tw) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T> *sm = reinterpret_cast<cx<T> *>(smem_raw);
+    using word_t = typename BitsWord<COLS>::type;
+    const uint32_t col = threadIdx.x % COLS, tq = threadIdx.x / COLS;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t S = L >> ilog2(LEN);
+    const uint64_t u0 = (uint64_t)blockIdx.x * COLS;
+    const uint64_t u = u0 + col;
+    const uint32_t ia = 2 * blockIdx.y, ib = ia + 1;
+    const bool has_b = ib < nblocks;
+    const BlockDev ba_ = blocks[ia];
+    const BlockDev bb_ = blocks[has_b ? ib : ia];
+    const cx<T> *w = W + (uint64_t)blockIdx.y * L;
+    cx<T> v[E];
+#pragma unroll
+    for (int s = 0; s < E; ++s) v[s] = w[(uint64_t)idx_e<LEN, E>(tq, s) * S + u];
+    twiddle_chain<T, true, E>(v, tw, (uint32_t)(tq * u), (uint32_t)((LEN / E) * u));
+    cta_fft<T, LEN, COLS, E, true>(sm, v, tq, col, tw);
+    const uint32_t popa = popc[ba_.id];
+    const uint32_t popb = has_b ? popc[bb_.id] : 0u;
+    word_t *oa = reinterpret_cast<word_t *>(ba_.out);
+    word_t *ob = reinterpret_cast<word_t *>(bb_.out);
+    const uint64_t nca = ((ba_.m + 63) >> 6) * (64 / COLS), ncb = ((bb_.m + 63) >> 6) * (64 / COLS);
+    typename Enc<T>::M ma = 0, mb = 0;
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+        const uint64_t t1 = idx_r0<LEN, E>(tq, s);
+        const uint64_t i = t1 * S + u;
+        bool bit_a, bit_b, xa, xb;
+        typename Enc<T>::M da = 0, db = 0;
+        // decode each block with its own m (validity differs between the two blocks)
+        Enc<T>::decode(v[s], popa, popb, i < ba_.m, bit_a, xb, ma, da);
+        Enc<T>::decode(v[s], popa, popb, has_b && i < bb_.m, xa, bit_b, db, mb);
+        const uint32_t wa = __ballot_sync(0xffffffffu, bit_a);
+        const uint32_t wb = __ballot_sync(0xffffffffu, bit_b);
+        if (col == 0) {
+            const uint64_t ci = (t1 * S + u0) / COLS;
+            const uint32_t msk = (COLS == 32) ? 0xffffffffu : ((1u << COLS) - 1u);
+            if (ci < nca) oa[ci] = (word_t)((wa >> lane) & msk);
+            if (has_b && ci < ncb) ob[ci] = (word_t)((wb >> lane) & msk);
+        }
+    }
+    uint32_t fa = __float_as_uint(margin_to_float(ma)), fb = __float_as_uint(margin_to_float(mb));
+    fa = __reduce_max_sync(0xffffffffu, fa);
+    fb = __reduce_max_sync(0xffffffffu, fb);
+    if (lane == 0) {
+        atomicMax(margin_bits + ba_.id, fa);
+        if (has_b) atomicMax(margin_bits + bb_.id, fb);
+    }
+}
+
+}  // namespace pa

@@ -6,10 +6,22 @@
 
 namespace pa {
 
+// Opt a kernel into more than 48 KB of dynamic shared memory, once per kernel
+// and device: later launches (and launches inside a stream capture) make no
+// attribute call.
+bool smem_configured(const void *kernel, int device);
+void smem_mark_configured(const void *kernel, int device);
+
 template <typename K>
 static cudaError_t set_smem(K kernel, size_t bytes) {
     if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+    const void *key = reinterpret_cast<const void *>(kernel);
+    if (smem_configured(key, dev)) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) smem_mark_configured(key, dev);
+    return e;
 }
 
 template <typename T, int LEN, int COLS>
@@ -135,5 +147,62 @@ cudaError_t launch_inv_bits(int lgLEN, const cx<T> *W, uint64_t L, uint64_t m, u
                                           cudaStream_t);                                                        \
     template cudaError_t launch_inv_bits<T>(int, const cx<T> *, uint64_t, uint64_t, uint32_t, const uint32_t *,  \
                                             uint32_t *, uint64_t *, uint64_t, uint32_t, TwTab<T>, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_fwd_keyseed(int lgLEN, const BlockDev *blocks, uint32_t nblocks, cx<T> *W, uint64_t L,
+                               TwTab<T> tw, cudaStream_t st) {
+    constexpr int E = Shape<T>::E, COLS = Shape<T>::COLS;
+    return by_len<kMinLgStrided, kMaxLgStrided>(lgLEN, [&](auto c) {
+        constexpr int LEN = decltype(c)::value;
+        auto kern = k_fwd_keyseed<T, LEN, COLS, E>;
+        constexpr size_t sb = smem_bytes<T, LEN, COLS>();
+        cudaError_t e = set_smem(kern, sb);
+        if (e != cudaSuccess) return e;
+        dim3 grid((unsigned)((L / LEN) / COLS), nblocks);
+        kern<<<grid, COLS * LEN / E, sb, st>>>(blocks, W, L, tw);
+        return cudaGetLastError();
+    });
+}
+
+template <typename T>
+cudaError_t launch_middle_split(int lgLEN, const cx<T> *Wf, cx<T> *Wi, uint64_t L, uint32_t nblocks, uint32_t lgL1,
+                                uint32_t lgM, TwTab<T> tw, cudaStream_t st) {
+    constexpr int E = Shape<T>::E;
+    return by_len<kMinLgMiddle, MaxLgSplit<T>::v>(lgLEN, [&](auto c) {
+        constexpr int LEN = decltype(c)::value;
+        auto kern = k_middle_split<T, LEN, E>;
+        constexpr size_t sb = 2 * smem_bytes<T, LEN, 1>();
+        cudaError_t e = set_smem(kern, sb);
+        if (e != cudaSuccess) return e;
+        const uint32_t R = (uint32_t)(L / LEN);
+        dim3 grid(R / 2 + 1, (nblocks + 1) / 2);
+        kern<<<grid, 2 * (LEN / E), sb, st>>>(Wf, Wi, L, nblocks, lgL1, lgM, tw, (T)(1.0 / (double)L));
+        return cudaGetLastError();
+    });
+}
+
+template <typename T>
+cudaError_t launch_inv_bits_blocks(int lgLEN, const cx<T> *Wi, uint64_t L, const BlockDev *blocks, uint32_t nblocks,
+                                   const uint32_t *popc, uint32_t *margin_bits, TwTab<T> tw, cudaStream_t st) {
+    constexpr int E = Shape<T>::E, COLS = Shape<T>::COLS;
+    return by_len<kMinLgStrided, kMaxLgStrided>(lgLEN, [&](auto c) {
+        constexpr int LEN = decltype(c)::value;
+        auto kern = k_inv_bits_blocks<T, LEN, COLS, E>;
+        constexpr size_t sb = smem_bytes<T, LEN, COLS>();
+        cudaError_t e = set_smem(kern, sb);
+        if (e != cudaSuccess) return e;
+        dim3 grid((unsigned)((L / LEN) / COLS), (nblocks + 1) / 2);
+        kern<<<grid, COLS * LEN / E, sb, st>>>(Wi, L, blocks, nblocks, popc, margin_bits, tw);
+        return cudaGetLastError();
+    });
+}
+
+#define PA_INSTANTIATE_UNEVEN(T)                                                                                 \
+    template cudaError_t launch_fwd_keyseed<T>(int, const BlockDev *, uint32_t, cx<T> *, uint64_t, TwTab<T>,     \
+                                               cudaStream_t);                                                   \
+    template cudaError_t launch_middle_split<T>(int, const cx<T> *, cx<T> *, uint64_t, uint32_t, uint32_t,       \
+                                                uint32_t, TwTab<T>, cudaStream_t);                               \
+    template cudaError_t launch_inv_bits_blocks<T>(int, const cx<T> *, uint64_t, const BlockDev *, uint32_t,     \
+                                                   const uint32_t *, uint32_t *, TwTab<T>, cudaStream_t);
 
 }  // namespace pa

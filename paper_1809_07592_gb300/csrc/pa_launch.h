@@ -49,4 +49,22 @@ cudaError_t launch_inv_bits(int lgLEN, const cx<T> *W, uint64_t L, uint64_t m, u
                             const uint32_t *popc, uint32_t *margin_bits, uint64_t *out, uint64_t ostride,
                             uint32_t pairs, TwTab<T> tw, cudaStream_t st);
 
+// ---- uneven batch (complex arithmetic only: the Eq. 5-10 split needs conjugation) ----
+struct BlockDev;
+template <typename T> struct MaxLgSplit;
+template <> struct MaxLgSplit<float> { static constexpr int v = 13; };
+template <> struct MaxLgSplit<double> { static constexpr int v = 12; };
+
+cudaError_t launch_prep_blocks(const BlockDev *blocks, uint32_t nblocks, uint32_t *popc, uint32_t *margin_bits,
+                               cudaStream_t st);
+template <typename T>
+cudaError_t launch_fwd_keyseed(int lgLEN, const BlockDev *blocks, uint32_t nblocks, cx<T> *W, uint64_t L,
+                               TwTab<T> tw, cudaStream_t st);
+template <typename T>
+cudaError_t launch_middle_split(int lgLEN, const cx<T> *Wf, cx<T> *Wi, uint64_t L, uint32_t nblocks, uint32_t lgL1,
+                                uint32_t lgM, TwTab<T> tw, cudaStream_t st);
+template <typename T>
+cudaError_t launch_inv_bits_blocks(int lgLEN, const cx<T> *Wi, uint64_t L, const BlockDev *blocks, uint32_t nblocks,
+                                   const uint32_t *popc, uint32_t *margin_bits, TwTab<T> tw, cudaStream_t st);
+
 }  // namespace pa

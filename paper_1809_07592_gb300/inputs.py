@@ -111,3 +111,24 @@ def uniform01(base_seed: int, stream_id: int, count: int) -> np.ndarray:
     """``count`` doubles in [0, 1) from the top 53 bits of a stream."""
     w = words(base_seed, stream_id, count)
     return (w >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
+
+
+STREAM_UNEVEN_N = 1_000_001
+STREAM_UNEVEN_M = 1_000_002
+
+
+def uneven_sizes(nblocks: int, base_seed: int = 0, lg_lo: float = 16.0, lg_hi: float = 24.0,
+                 ratio_lo: float = 0.05, ratio_hi: float = 0.6):
+    """(n, m) for an uneven batch: n = floor(2^u), u ~ U[lg_lo, lg_hi]; m = floor(r n), r ~ U[ratio_lo, ratio_hi], m >= 1."""
+    u = uniform01(base_seed, STREAM_UNEVEN_N, nblocks)
+    r = uniform01(base_seed, STREAM_UNEVEN_M, nblocks)
+    ns = np.floor(np.exp2(lg_lo + (lg_hi - lg_lo) * u)).astype(np.int64)
+    ms = np.maximum(1, np.floor((ratio_lo + (ratio_hi - ratio_lo) * r) * ns)).astype(np.int64)
+    ms = np.minimum(ms, ns)
+    return [(int(n), int(m)) for n, m in zip(ns, ms)]
+
+
+def uneven_block_inputs(sizes, base_seed: int = 0):
+    """Keys (stream 2b+2) and seeds (stream 2b+3) for block b of an uneven batch."""
+    return [(bernoulli_bits(base_seed, 2 * b + 2, n), bernoulli_bits(base_seed, 2 * b + 3, n + m - 1))
+            for b, (n, m) in enumerate(sizes)]
