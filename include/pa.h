@@ -192,6 +192,68 @@ int pa_uneven_class(const pa_uneven_t *batch, uint32_t c, uint32_t *nclasses, ui
 int pa_hash_uneven(const pa_block_desc_t *blocks, uint32_t nblocks, pa_dtype_t dtype, pa_stream_t stream,
                    pa_batch_info_t *info);
 
+/* ---------------------------------------------------------------------------------------
+ * Serving loop: continuous batching of blocks submitted one at a time.
+ * ------------------------------------------------------------------------------------- */
+
+typedef struct pa_server pa_server_t;
+
+typedef struct {
+    uint64_t hbm_cap_bytes;  /* admission cap on the device scratch of in-flight blocks (0: 40e9) */
+    pa_dtype_t dtype;        /* PA_FP32_GUARD or PA_FP64 (a zeroed struct selects PA_FP64) */
+    uint32_t max_queue;      /* queued + in-flight blocks before pa_submit returns PA_EAGAIN (0: 65536) */
+    uint32_t max_batch;      /* blocks admitted into one micro-batch (0: 64) */
+    uint32_t streams;        /* micro-batches in flight at once, one stream each (0: 4) */
+    float guard;             /* rounding-margin threshold (<= 0: 0.25) */
+} pa_server_cfg_t;
+
+typedef struct {
+    int32_t status;        /* PA_OK, or the error that ended this block */
+    int32_t mode;          /* pa_dtype_t that produced the bits */
+    float margin;          /* rounding margin of that mode */
+    uint32_t reserved;
+    uint64_t t_submit_ns;  /* steady-clock timestamps: pa_submit, admission, completion seen by the server */
+    uint64_t t_admit_ns;
+    uint64_t t_done_ns;
+} pa_result_t;
+
+typedef struct {
+    uint64_t submitted, admitted, completed, escalated, rejected, batches;
+    uint64_t queued;               /* waiting for admission now */
+    uint64_t inflight_bytes;       /* admitted scratch now */
+    uint64_t peak_inflight_bytes;  /* largest admitted scratch so far (never above the cap) */
+} pa_server_stats_t;
+
+/*
+ * pa_server_create -- start a serving loop on the current device (one worker thread).
+ * Blocks are admitted first-come first-served while the scratch of everything in flight
+ * (about 1.5 * L * element size per block) fits under cfg->hbm_cap_bytes; each admitted
+ * micro-batch is grouped by transform length and run like an uneven batch (Eq. 5-10 key+seed
+ * transforms) on the next free stream, so later arrivals run while earlier ones are on the
+ * device. Scratch comes from a dedicated stream-ordered memory pool. Thread-safe.
+ */
+int pa_server_create(const pa_server_cfg_t *cfg, pa_server_t **out);
+
+/*
+ * pa_submit -- queue one block; *ticket identifies it in pa_poll / pa_wait. The block's device
+ * buffers must stay valid until its result has been collected. Returns PA_EAGAIN when
+ * cfg->max_queue blocks are already queued or in flight, PA_EINVAL for bad descriptors or a
+ * block whose scratch alone exceeds the cap.
+ */
+int pa_submit(pa_server_t *server, const pa_block_desc_t *block, uint64_t *ticket);
+
+/* Non-blocking: PA_OK and *result when the ticket has completed (the ticket is then released),
+ * PA_EPENDING while it is queued or running, PA_EINVAL for an unknown or released ticket. */
+int pa_poll(pa_server_t *server, uint64_t ticket, pa_result_t *result);
+
+/* Blocking variant of pa_poll with a bound: PA_ETIMEOUT after timeout_ms. */
+int pa_wait(pa_server_t *server, uint64_t ticket, uint32_t timeout_ms, pa_result_t *result);
+
+int pa_server_stats(pa_server_t *server, pa_server_stats_t *stats);
+
+/* Finish every queued block, stop the worker and release the server. NULL is accepted. */
+int pa_server_destroy(pa_server_t *server);
+
 /*
  * Kernel timing (measurement support, no counterpart in the paper). When enabled,
  * every kernel launch of the plan is bracketed by CUDA events recorded on the

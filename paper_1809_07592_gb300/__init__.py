@@ -55,6 +55,22 @@ class BlockDesc(ctypes.Structure):
                 ("out", ctypes.c_void_p)]
 
 
+class ServerCfg(ctypes.Structure):
+    _fields_ = [("hbm_cap_bytes", ctypes.c_uint64), ("dtype", ctypes.c_int), ("max_queue", ctypes.c_uint32),
+                ("max_batch", ctypes.c_uint32), ("streams", ctypes.c_uint32), ("guard", ctypes.c_float)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("mode", ctypes.c_int32), ("margin", ctypes.c_float),
+                ("reserved", ctypes.c_uint32), ("t_submit_ns", ctypes.c_uint64), ("t_admit_ns", ctypes.c_uint64),
+                ("t_done_ns", ctypes.c_uint64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint64) for f in ("submitted", "admitted", "completed", "escalated", "rejected",
+                                               "batches", "queued", "inflight_bytes", "peak_inflight_bytes")]
+
+
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
 
@@ -94,13 +110,20 @@ def lib():
     L.pa_uneven_class.argtypes = [vp, u32, ctypes.POINTER(u32), ctypes.POINTER(u64), ctypes.POINTER(u32),
                                   ctypes.POINTER(u32), ctypes.POINTER(u32), ctypes.POINTER(u32)]
     L.pa_hash_uneven.argtypes = [bdp, u32, ctypes.c_int, vp, ctypes.POINTER(BatchInfo)]
+    L.pa_server_create.argtypes = [ctypes.POINTER(ServerCfg), ctypes.POINTER(vp)]
+    L.pa_submit.argtypes = [vp, bdp, ctypes.POINTER(u64)]
+    L.pa_poll.argtypes = [vp, u64, ctypes.POINTER(Result)]
+    L.pa_wait.argtypes = [vp, u64, u32, ctypes.POINTER(Result)]
+    L.pa_server_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+    L.pa_server_destroy.argtypes = [vp]
     L.pa_strerror.argtypes = [ctypes.c_int]
     L.pa_strerror.restype = ctypes.c_char_p
     L.pa_last_cuda_error.argtypes = []
     L.pa_last_cuda_error.restype = ctypes.c_char_p
     for name in ("pa_plan", "pa_plan_destroy", "pa_set_seed", "pa_hash_batch", "pa_plan_set_guard",
                  "pa_plan_shape", "pa_profile_enable", "pa_profile_read", "pa_uneven_create", "pa_uneven_update",
-                 "pa_uneven_run", "pa_uneven_set_guard", "pa_uneven_destroy", "pa_uneven_class", "pa_hash_uneven"):
+                 "pa_uneven_run", "pa_uneven_set_guard", "pa_uneven_destroy", "pa_uneven_class", "pa_hash_uneven",
+                 "pa_server_create", "pa_submit", "pa_poll", "pa_wait", "pa_server_stats", "pa_server_destroy"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -258,6 +281,50 @@ def pa_hash_uneven(blocks, dtype=PA_FP32_GUARD, stream=None, info: bool = False)
         return list(marg), list(mode), bi.escalated
     _check(lib().pa_hash_uneven(arr, nb, dtype, _stream_handle(stream), None), "pa_hash_uneven")
     return None
+
+
+def pa_server_create(hbm_cap_bytes: int = 0, dtype=PA_FP32_GUARD, max_queue: int = 0, max_batch: int = 0,
+                     streams: int = 0, guard: float = 0.25) -> int:
+    if isinstance(dtype, str):
+        dtype = DTYPES[dtype]
+    cfg = ServerCfg(hbm_cap_bytes, dtype, max_queue, max_batch, streams, guard)
+    h = ctypes.c_void_p()
+    _check(lib().pa_server_create(ctypes.byref(cfg), ctypes.byref(h)), "pa_server_create")
+    return h.value
+
+
+def pa_submit(server: int, n: int, m: int, key, seed, out) -> int:
+    """Queue one block; returns its ticket. Raises PAError (code PA_EAGAIN when the queue is full)."""
+    d = BlockDesc(n, m, _ptr(key), _ptr(seed), _ptr(out))
+    t = ctypes.c_uint64()
+    _check(lib().pa_submit(server, ctypes.byref(d), ctypes.byref(t)), "pa_submit")
+    return t.value
+
+
+def pa_poll(server: int, ticket: int):
+    """Result struct when done, None while pending."""
+    r = Result()
+    rc = lib().pa_poll(server, ticket, ctypes.byref(r))
+    if rc == PA_EPENDING:
+        return None
+    _check(rc, "pa_poll")
+    return r
+
+
+def pa_wait(server: int, ticket: int, timeout_ms: int):
+    r = Result()
+    _check(lib().pa_wait(server, ticket, timeout_ms, ctypes.byref(r)), "pa_wait")
+    return r
+
+
+def pa_server_stats(server: int) -> dict:
+    st = ServerStats()
+    _check(lib().pa_server_stats(server, ctypes.byref(st)), "pa_server_stats")
+    return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+
+def pa_server_destroy(server: int) -> None:
+    _check(lib().pa_server_destroy(server), "pa_server_destroy")
 
 
 class Plan:

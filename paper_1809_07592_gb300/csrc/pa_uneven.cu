@@ -17,11 +17,14 @@
 #include <vector>
 
 #include "pa.h"
+#include "pa_blocks.h"
 #include "pa_internal.h"
 #include "pa_kernels.cuh"
 #include "pa_launch.h"
 
 using namespace pa;
+using pa::blocks::ClassRun;
+using pa::blocks::Split;
 
 namespace {
 
@@ -30,10 +33,6 @@ namespace {
         cudaError_t e_ = (call);                                         \
         if (e_ != cudaSuccess) return pa_internal_cuda_fail(e_, #call);  \
     } while (0)
-
-struct Split {
-    int lg1 = 0, lgM = 0, lgI = 0;  // strided, middle strided (0: two levels), innermost
-};
 
 struct UClass {
     int lgL = 0;
@@ -47,10 +46,25 @@ struct UClass {
     uint32_t B = 0;
     cudaStream_t st = nullptr;
     cudaEvent_t done = nullptr;
+    ClassRun run(const Split &s) const {
+        ClassRun r;
+        r.lgL = lgL;
+        r.L = L;
+        r.sp = s;
+        r.d_blocks = d_blocks;
+        r.nb = (uint32_t)ids.size();
+        r.Wf = Wf;
+        r.Wi = Wi;
+        r.spec = spec;
+        r.tw_hi = tw_hi;
+        r.tw_lo = tw_lo;
+        r.B = B;
+        return r;
+    }
 };
 
 // ---------------------------------------------------------------------------
-// Autotuner: best split per (lgL, dtype), measured on the first batch that needs it.
+// Autotuner cache: best split per (lgL, dtype), measured on the first batch that needs it.
 std::mutex g_tune_mu;
 std::map<std::pair<int, int>, Split> g_tune;
 bool g_tune_loaded = false;
@@ -67,25 +81,9 @@ void tune_load_locked() {
     std::fclose(f);
 }
 
-void tune_store_locked(int lgL, int dt, const Split &s) {
-    g_tune[{lgL, dt}] = s;
-    const char *path = std::getenv("PA_TUNE_CACHE");
-    if (!path) return;
-    FILE *f = std::fopen(path, "a");
-    if (!f) return;
-    std::fprintf(f, "%d %d %d %d %d\n", lgL, dt, s.lg1, s.lgM, s.lgI);
-    std::fclose(f);
-}
-
-std::vector<Split> candidates(int lgL, int maxInner) {
-    std::vector<Split> two, three;
-    for (int lg1 = kMinLgStrided; lg1 <= kMaxLgStrided; ++lg1) {
-        const int in2 = lgL - lg1;
-        if (in2 >= kMinLgMiddle && in2 <= maxInner) two.push_back(Split{lg1, 0, in2});
-        const int in3 = lgL - lg1 - kMinLgStrided;
-        if (in3 >= kMinLgMiddle && in3 <= maxInner) three.push_back(Split{lg1, kMinLgStrided, in3});
-    }
-    return two.empty() ? three : two;
+int max_inner(pa_dtype_t dtype) {
+    return dtype == PA_FP32_GUARD ? MaxLgSplit<float>::v : dtype == PA_FP64 ? MaxLgSplit<double>::v
+                                                                              : MaxLgMiddle<Zp>::v;
 }
 
 }  // namespace
@@ -111,7 +109,7 @@ struct pa_uneven {
 namespace {
 
 template <typename T>
-TwTab<T> tw_of(const UClass &c) {
+TwTab<T> tw_of(const ClassRun &c) {
     TwTab<T> t;
     t.hi = static_cast<const cx<T> *>(c.tw_hi);
     t.lo = static_cast<const cx<T> *>(c.tw_lo);
@@ -122,7 +120,7 @@ TwTab<T> tw_of(const UClass &c) {
 
 // Middle strided pass over `slots` consecutive slots, chunked to the grid's y limit.
 template <typename T>
-int mid_chunks(const UClass &c, bool inverse, cx<T> *W, uint32_t slots, cudaStream_t st) {
+int mid_chunks(const ClassRun &c, bool inverse, cx<T> *W, uint32_t slots, cudaStream_t st) {
     const uint32_t nblk = (uint32_t)(c.L >> (c.sp.lgM + c.sp.lgI));
     const uint32_t per = 65535u / nblk;
     const TwTab<T> tw = tw_of<T>(c);
@@ -135,81 +133,64 @@ int mid_chunks(const UClass &c, bool inverse, cx<T> *W, uint32_t slots, cudaStre
 
 // The whole chain of one class (complex modes).
 template <typename T>
-int run_class_complex(pa_uneven_t *u, const UClass &c, const Split &sp, cudaStream_t st) {
-    UClass cc = c;
-    cc.sp = sp;
-    const uint32_t nb = (uint32_t)c.ids.size();
-    const TwTab<T> tw = tw_of<T>(cc);
+int run_class_complex(const ClassRun &c, uint32_t *popc, uint32_t *marg, cudaStream_t st) {
+    const Split &sp = c.sp;
+    const uint32_t nb = c.nb;
+    const TwTab<T> tw = tw_of<T>(c);
     cx<T> *Wf = static_cast<cx<T> *>(c.Wf), *Wi = static_cast<cx<T> *>(c.Wi);
-    U_CUDA(launch_prep_blocks(c.d_blocks, nb, u->popc, u->marg, st));
+    U_CUDA(launch_prep_blocks(c.d_blocks, nb, popc, marg, st));
     U_CUDA(launch_fwd_keyseed<T>(sp.lg1, c.d_blocks, nb, Wf, c.L, tw, st));
     if (sp.lgM) {
-        int rc = mid_chunks<T>(cc, false, Wf, nb, st);
+        int rc = mid_chunks<T>(c, false, Wf, nb, st);
         if (rc != PA_OK) return rc;
     }
     U_CUDA(launch_middle_split<T>(sp.lgI, Wf, Wi, c.L, nb, (uint32_t)sp.lg1, (uint32_t)sp.lgM, tw, st));
     if (sp.lgM) {
-        int rc = mid_chunks<T>(cc, true, Wi, (nb + 1) / 2, st);
+        int rc = mid_chunks<T>(c, true, Wi, (nb + 1) / 2, st);
         if (rc != PA_OK) return rc;
     }
-    U_CUDA(launch_inv_bits_blocks<T>(sp.lg1, Wi, c.L, c.d_blocks, nb, u->popc, u->marg, tw, st));
+    U_CUDA(launch_inv_bits_blocks<T>(sp.lg1, Wi, c.L, c.d_blocks, nb, popc, marg, tw, st));
     return PA_OK;
 }
 
 // NTT mode: per block, seed transform into the class's spectrum slot, then the key.
-int run_class_ntt(pa_uneven_t *u, const UClass &c, cudaStream_t st) {
+int run_class_ntt(const ClassRun &c, const pa_block_desc_t *hb, const uint32_t *ids, uint32_t *popc,
+                  uint32_t *marg, cudaStream_t st) {
     const TwTab<Zp> tw = tw_of<Zp>(c);
     cx<Zp> *W = static_cast<cx<Zp> *>(c.Wf), *spec = static_cast<cx<Zp> *>(c.spec);
     const Split &sp = c.sp;
     const uint64_t L = c.L;
-    cx<Zp> invL = 1;
-    {  // L^-1 mod p = 2^(192 - lgL)
-        const int k = 192 - c.lgL;
-        invL = zp_pow2(k);
-    }
-    for (uint32_t i = 0; i < c.ids.size(); ++i) {
-        const pa_block_desc_t &b = u->blocks[c.ids[i]];
+    const cx<Zp> invL = zp_pow2(192 - c.lgL);  // L^-1 mod p = 2^(192 - lgL)
+    for (uint32_t i = 0; i < c.nb; ++i) {
+        const pa_block_desc_t &b = hb[ids[i]];
         const uint64_t kw = (b.n + 63) / 64;
         U_CUDA(launch_fwd_seed<Zp>(sp.lg1, b.seed, b.n, b.m, W, L, tw, st));
         if (sp.lgM) U_CUDA(launch_mid<Zp>(sp.lgM, false, W, L, (uint32_t)sp.lgI, 1, tw, st));
         U_CUDA(launch_middle<Zp>(sp.lgI, 1, W, spec, L, 1, tw, invL, st));
-        U_CUDA(launch_prep(b.key, 1, kw, b.n, u->popc + c.ids[i], u->marg + c.ids[i], st));
+        U_CUDA(launch_prep(b.key, 1, kw, b.n, popc + ids[i], marg + ids[i], st));
         U_CUDA(launch_fwd_keys<Zp>(sp.lg1, b.key, 1, kw, b.n, W, L, 1, tw, st));
         if (sp.lgM) U_CUDA(launch_mid<Zp>(sp.lgM, false, W, L, (uint32_t)sp.lgI, 1, tw, st));
         U_CUDA(launch_middle<Zp>(sp.lgI, 0, W, spec, L, 1, tw, (cx<Zp>)1, st));
         if (sp.lgM) U_CUDA(launch_mid<Zp>(sp.lgM, true, W, L, (uint32_t)sp.lgI, 1, tw, st));
-        U_CUDA(launch_inv_bits<Zp>(sp.lg1, W, L, b.m, 1, u->popc + c.ids[i], u->marg + c.ids[i], b.out,
-                                   (b.m + 63) / 64, 1, tw, st));
+        U_CUDA(launch_inv_bits<Zp>(sp.lg1, W, L, b.m, 1, popc + ids[i], marg + ids[i], b.out, (b.m + 63) / 64, 1, tw,
+                                   st));
     }
     return PA_OK;
 }
 
 int run_class(pa_uneven_t *u, const UClass &c, cudaStream_t st) {
-    if (u->dtype == PA_FP32_GUARD) return run_class_complex<float>(u, c, c.sp, st);
-    if (u->dtype == PA_FP64) return run_class_complex<double>(u, c, c.sp, st);
-    return run_class_ntt(u, c, st);
+    if (u->dtype == PA_NTT64) return run_class_ntt(c.run(c.sp), u->blocks.data(), c.ids.data(), u->popc, u->marg, st);
+    return pa::blocks::run_complex(u->dtype, c.run(c.sp), u->popc, u->marg, st);
 }
 
 // Choose a class's split: cached, else time every candidate on the class's own data.
 int tune_class(pa_uneven_t *u, UClass &c) {
-    const int maxInner = u->dtype == PA_FP32_GUARD ? MaxLgSplit<float>::v
-                         : u->dtype == PA_FP64     ? MaxLgSplit<double>::v
-                                                   : MaxLgMiddle<Zp>::v;
-    std::vector<Split> cand = candidates(c.lgL, maxInner);
+    std::vector<Split> cand = pa::blocks::candidates(c.lgL, u->dtype);
     if (cand.empty()) return PA_EUNSUPPORTED;
-    {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        tune_load_locked();
-        auto it = g_tune.find({c.lgL, (int)u->dtype});
-        if (it != g_tune.end()) {
-            c.sp = it->second;
-            return PA_OK;
-        }
-    }
+    if (pa::blocks::cached_split(c.lgL, u->dtype, &c.sp)) return PA_OK;
     if (cand.size() == 1 || u->dtype == PA_NTT64) {
-        c.sp = cand[cand.size() / 2];
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        tune_store_locked(c.lgL, (int)u->dtype, c.sp);
+        c.sp = pa::blocks::default_split(c.lgL, u->dtype);
+        pa::blocks::store_split(c.lgL, u->dtype, c.sp);
         return PA_OK;
     }
     cudaEvent_t a, b;
@@ -221,8 +202,7 @@ int tune_class(pa_uneven_t *u, UClass &c) {
         float total = 0.f;
         for (int rep = 0; rep < 3; ++rep) {
             U_CUDA(cudaEventRecord(a, c.st));
-            int rc = (u->dtype == PA_FP32_GUARD) ? run_class_complex<float>(u, c, sp, c.st)
-                                                 : run_class_complex<double>(u, c, sp, c.st);
+            int rc = pa::blocks::run_complex(u->dtype, c.run(sp), u->popc, u->marg, c.st);
             if (rc != PA_OK) return rc;
             U_CUDA(cudaEventRecord(b, c.st));
             U_CUDA(cudaEventSynchronize(b));
@@ -238,8 +218,7 @@ int tune_class(pa_uneven_t *u, UClass &c) {
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     c.sp = bestsp;
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    tune_store_locked(c.lgL, (int)u->dtype, c.sp);
+    pa::blocks::store_split(c.lgL, u->dtype, c.sp);
     return PA_OK;
 }
 
@@ -266,11 +245,7 @@ void free_uneven(pa_uneven_t *u) {
     delete u;
 }
 
-int lg_length(const pa_block_desc_t &b) {
-    int lgL = 12;
-    while ((1ull << lgL) < b.n + b.m - 1) ++lgL;
-    return lgL;
-}
+int lg_length(const pa_block_desc_t &b) { return pa::blocks::lg_length(b.n, b.m); }
 
 bool desc_ok(const pa_block_desc_t &b) {
     if (b.n == 0 || b.m == 0 || b.m > b.n || b.n > (1ull << 27)) return false;
@@ -321,6 +296,83 @@ int capture_graph(pa_uneven_t *u) {
 }
 
 }  // namespace
+
+namespace pa {
+namespace blocks {
+
+int lg_length(uint64_t n, uint64_t m) {
+    int lgL = 12;
+    while ((1ull << lgL) < n + m - 1) ++lgL;
+    return lgL;
+}
+
+size_t scratch_per_block(int lgL, pa_dtype_t dtype) {
+    const size_t L = (size_t)1 << lgL;
+    if (dtype == PA_NTT64) return 2 * L * 8;
+    const size_t e = dtype == PA_FP32_GUARD ? sizeof(float2) : sizeof(double2);
+    return L * e + (L * e + 1) / 2 + sizeof(BlockDev) + 8;  // forward slot, half an inverse slot, descriptor, counters
+}
+
+int run_complex(pa_dtype_t dtype, const ClassRun &c, uint32_t *popc, uint32_t *marg, cudaStream_t st) {
+    return dtype == PA_FP32_GUARD ? run_class_complex<float>(c, popc, marg, st)
+                                  : run_class_complex<double>(c, popc, marg, st);
+}
+
+int run_ntt(const ClassRun &c, const pa_block_desc_t *hb, const uint32_t *ids, uint32_t *popc, uint32_t *marg,
+            cudaStream_t st) {
+    return run_class_ntt(c, hb, ids, popc, marg, st);
+}
+
+std::vector<Split> candidates(int lgL, pa_dtype_t dtype) {
+    const int maxI = max_inner(dtype);
+    std::vector<Split> two, three;
+    for (int lg1 = kMinLgStrided; lg1 <= kMaxLgStrided; ++lg1) {
+        const int in2 = lgL - lg1;
+        if (in2 >= kMinLgMiddle && in2 <= maxI) two.push_back(Split{lg1, 0, in2});
+        const int in3 = lgL - lg1 - kMinLgStrided;
+        if (in3 >= kMinLgMiddle && in3 <= maxI) three.push_back(Split{lg1, kMinLgStrided, in3});
+    }
+    return two.empty() ? three : two;
+}
+
+Split default_split(int lgL, pa_dtype_t dtype) {
+    std::vector<Split> c = candidates(lgL, dtype);
+    if (c.empty()) return Split{};
+    // prefer an innermost transform near 2^12 (fits one CTA with room for two per SM)
+    Split best = c[0];
+    int bestd = 1 << 30;
+    for (const Split &s : c) {
+        const int d = s.lgI > 12 ? s.lgI - 12 : 12 - s.lgI;
+        if (d < bestd) {
+            bestd = d;
+            best = s;
+        }
+    }
+    return best;
+}
+
+bool cached_split(int lgL, pa_dtype_t dtype, Split *out) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load_locked();
+    auto it = g_tune.find({lgL, (int)dtype});
+    if (it == g_tune.end()) return false;
+    *out = it->second;
+    return true;
+}
+
+void store_split(int lgL, pa_dtype_t dtype, const Split &s) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[{lgL, (int)dtype}] = s;
+    const char *path = std::getenv("PA_TUNE_CACHE");
+    if (!path) return;
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%d %d %d %d %d\n", lgL, (int)dtype, s.lg1, s.lgM, s.lgI);
+    std::fclose(f);
+}
+
+}  // namespace blocks
+}  // namespace pa
 
 extern "C" {
 

@@ -132,3 +132,27 @@ def uneven_block_inputs(sizes, base_seed: int = 0):
     """Keys (stream 2b+2) and seeds (stream 2b+3) for block b of an uneven batch."""
     return [(bernoulli_bits(base_seed, 2 * b + 2, n), bernoulli_bits(base_seed, 2 * b + 3, n + m - 1))
             for b, (n, m) in enumerate(sizes)]
+
+
+STREAM_SERVE_N = 1_000_003
+STREAM_SERVE_M = 1_000_004
+STREAM_SERVE_T = 1_000_005
+SERVE_N_CHOICES = (1 << 18, 1_000_000, 1 << 22, 1 << 24)
+SERVE_N_WEIGHTS = (0.4, 0.3, 0.2, 0.1)
+
+
+def serving_requests(count: int, rate_per_s: float, base_seed: int = 0, ratio_lo: float = 0.1,
+                     ratio_hi: float = 0.5):
+    """Arrival times (s, Poisson process of the given rate) and (n, m) for a serving run.
+
+    n is drawn from SERVE_N_CHOICES with SERVE_N_WEIGHTS, m = floor(U[ratio_lo, ratio_hi] * n).
+    """
+    u_n = uniform01(base_seed, STREAM_SERVE_N, count)
+    u_m = uniform01(base_seed, STREAM_SERVE_M, count)
+    u_t = uniform01(base_seed, STREAM_SERVE_T, count)
+    cum = np.cumsum(SERVE_N_WEIGHTS)
+    idx = np.searchsorted(cum, u_n * cum[-1], side="right")
+    ns = np.array(SERVE_N_CHOICES, dtype=np.int64)[np.minimum(idx, len(SERVE_N_CHOICES) - 1)]
+    ms = np.maximum(1, np.floor((ratio_lo + (ratio_hi - ratio_lo) * u_m) * ns)).astype(np.int64)
+    gaps = -np.log1p(-u_t) / rate_per_s  # exponential inter-arrival times
+    return np.cumsum(gaps), [(int(n), int(m)) for n, m in zip(ns, ms)]

@@ -203,3 +203,18 @@ def test_argument_errors():
         pa.pa_hash_batch(plan.handle, keys[:, 1:], 2, 16, out, 2)  # misaligned
     assert e.value.code == pa.PA_EINVAL
     plan.close()
+
+
+@pytest.mark.parametrize("dtype", MODES, ids=MODE_ID.get)
+def test_long_block_2p27(dtype):
+    """The long single block: n = 2^27, m = 2^24, transform length 2^28, seed spectrum resident."""
+    n, m = 1 << 27, 1 << 24
+    key, seed = inputs.block_inputs(n, m, base_seed=0)
+    got, marg, mode, esc, shape = run(n, m, dtype, key[None, :], seed)
+    assert shape[0] == 1 << 28 and shape[3] > 1
+    rows = sample_rows(m, 120, seed=27)
+    exp = oracle.toeplitz_rows(n, m, seed, key, rows)
+    np.testing.assert_array_equal(unpack_rows(got, m)[0][rows.astype(np.int64)], exp)
+    if dtype == pa.PA_FP32_GUARD:
+        assert mode[0] in (pa.PA_FP32_GUARD, pa.PA_FP64)  # the guard may hand it to FP64
+    assert marg[0] < 0.25
