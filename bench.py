@@ -188,7 +188,7 @@ def run_reference(args):
     threads = os.cpu_count() or 1
     n, m = 1 << 20, 1 << 18
     key, seed = inputs.block_inputs(n, m, base_seed=0, key_stream=2)
-    rows = 4096
+    rows = 1024
     oracle.toeplitz_row_range(n, m, seed, key, 0, 256, threads)  # build + warm
     for _ in range(args.warmup):
         oracle.toeplitz_row_range(n, m, seed, key, 0, 256, threads)
@@ -212,10 +212,109 @@ def run_reference(args):
     return 0
 
 
+def _dev_words(torch, words, device):
+    w = np.zeros(words.size + (words.size & 1), dtype=np.uint64)
+    w[: words.size] = words
+    return torch.from_numpy(w.view(np.int64)).to(device)
+
+
+def measure_uneven(pa, inputs, torch, dev, reps=5):
+    """256 blocks, n log-uniform in [2^16, 2^24], m/n in [0.05, 0.6], per-block seeds, graph replay."""
+    sizes = inputs.uneven_sizes(256, base_seed=0)
+    blocks = []
+    for b, (n, m) in enumerate(sizes):
+        k = _dev_words(torch, inputs.bernoulli_bits(0, 2 * b + 2, n), dev)
+        sd = _dev_words(torch, inputs.bernoulli_bits(0, 2 * b + 3, n + m - 1), dev)
+        ow = (m + 63) // 64
+        blocks.append((n, m, k, sd, torch.empty(ow + (ow & 1), dtype=torch.int64, device=dev)))
+    h = pa.pa_uneven_create(blocks, pa.PA_FP32_GUARD, use_graph=True)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        pa.pa_uneven_run(h, len(blocks), stream)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pa.pa_uneven_run(h, len(blocks), stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    ms = statistics.median(ts)
+    classes = pa.pa_uneven_classes(h)
+    pa.pa_uneven_destroy(h)
+    bits = sum(n for n, _ in sizes)
+    return {"value": bits / (ms * 1e-3) / 1e6, "unit": "Mbit/s", "ms_per_batch": ms, "blocks": len(sizes),
+            "mode": "FP32_GUARD", "graph": True,
+            "classes": [{"L": c[0], "split": [c[1], c[2], c[3]], "blocks": c[4]} for c in classes]}
+
+
+def measure_serving(pa, inputs, torch, dev, rate=5000.0, seconds=1.0):
+    """Poisson arrivals, n from {2^18, 1e6, 2^22, 2^24} w.p. {0.4, 0.3, 0.2, 0.1}, m/n in [0.1, 0.5], 40 GB cap."""
+    pool = {}
+    for n in inputs.SERVE_N_CHOICES:
+        pool[n] = []
+        for j in range(8):
+            k = _dev_words(torch, inputs.bernoulli_bits(9, 2 * j + 2, n), dev)
+            sd = _dev_words(torch, inputs.bernoulli_bits(9, 2 * j + 3, n + n // 2), dev)
+            pool[n].append((k, sd, torch.empty((n // 2 + 63) // 64 + 2, dtype=torch.int64, device=dev)))
+    srv = pa.pa_server_create(hbm_cap_bytes=40 * 10**9, dtype=pa.PA_FP32_GUARD)
+    warm = [pa.pa_submit(srv, n, n // 4, *pool[n][0]) for n in inputs.SERVE_N_CHOICES]
+    for t in warm:
+        pa.pa_wait(srv, t, 60000)
+    count = int(rate * seconds)
+    times, sizes = inputs.serving_requests(count, rate, base_seed=1)
+    t0 = time.perf_counter()
+    tickets = []
+    for i, (t, (n, m)) in enumerate(zip(times, sizes)):
+        while time.perf_counter() - t0 < t:
+            pass
+        tickets.append(pa.pa_submit(srv, n, m, *pool[n][i % 8]))
+    res = [pa.pa_wait(srv, t, 120000) for t in tickets]
+    st = pa.pa_server_stats(srv)
+    pa.pa_server_destroy(srv)
+    lat = np.array([(r.t_done_ns - r.t_submit_ns) / 1e6 for r in res])
+    span = (max(r.t_done_ns for r in res) - min(r.t_submit_ns for r in res)) / 1e9
+    bits = sum(n for n, _ in sizes)
+    return {"value": bits / span / 1e6, "unit": "Mbit/s", "offered_mbit_s": bits / times[-1] / 1e6,
+            "arrival_rate_per_s": rate, "requests": count, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()), "hbm_cap_bytes": 40 * 10**9,
+            "peak_inflight_bytes": st["peak_inflight_bytes"], "micro_batches": st["batches"],
+            "escalated": st["escalated"], "mode": "FP32_GUARD"}
+
+
+def measure_long_block(pa, inputs, torch, dev, reps=3):
+    """n = 2^27, m = 2^24 (transform length 2^28), one block, seed spectrum resident, per mode."""
+    n, m = 1 << 27, 1 << 24
+    key, seed = inputs.block_inputs(n, m, base_seed=0)
+    kd, sd = _dev_words(torch, key, dev), _dev_words(torch, seed, dev)
+    ow = (m + 63) // 64
+    out = torch.empty((1, ow + (ow & 1)), dtype=torch.int64, device=dev)
+    res = {}
+    stream = torch.cuda.current_stream()
+    for name, dt in (("fp32_guard", pa.PA_FP32_GUARD), ("fp64", pa.PA_FP64), ("ntt64", pa.PA_NTT64)):
+        plan = pa.Plan(n, m, dt)
+        plan.set_seed(sd)
+        pa.pa_hash_batch(plan.handle, kd.view(1, -1), 1, kd.numel(), out, out.shape[1], stream)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pa.pa_hash_batch(plan.handle, kd.view(1, -1), 1, kd.numel(), out, out.shape[1], stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        ms = statistics.median(ts)
+        res[name] = {"value": n / (ms * 1e-3) / 1e6, "unit": "Mbit/s", "ms": ms}
+        plan.close()
+    return res
+
+
 def run_ours(args):
     import torch
     import paper_1809_07592_gb300 as pa
-    from paper_1809_07592_gb300 import inputs
+    from paper_1809_07592_gb300 import inputs, replicas
 
     rank, world, local = dist_env()
     if world > 1:
@@ -229,7 +328,7 @@ def run_ours(args):
 
     # --- inputs resident in HBM; one plan + seed per (n, m) -------------------------------------------
     cases = []
-    base = 1000 * rank  # each replica draws its own keys
+    base = replicas.rank_base_seed(rank)  # each replica draws its own keys
     for n, m in subconfigs():
         seed = inputs.bernoulli_bits(base, inputs.STREAM_SEED, n + m - 1)
         keys = inputs.batch_keys(n, NKEYS, base_seed=base)
@@ -311,13 +410,8 @@ def run_ours(args):
     traffic = ncu_traffic(dom_name)
 
     bits_per_step = sum(c["n"] for c in cases) * NKEYS
-    t_step = statistics.mean(step_ms)
-    total = torch.tensor([t_step], dtype=torch.float64, device=dev)
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(total, op=dist.ReduceOp.MAX)
-    t_max = float(total.item())
-    value = bits_per_step * world / (t_max * 1e-3) / 1e6
+    t_max = replicas.max_over_ranks(statistics.mean(step_ms), dev)
+    value = replicas.whole_job_rate(bits_per_step, world, t_max * 1e-3) / 1e6
 
     # --- plain single-key FP64 form on the same sizes (the other side of the metric) ---------------
     fp64 = []
@@ -358,11 +452,14 @@ def run_ours(args):
         torch.cuda.synchronize()
         if it >= args.warmup:
             e2e_ms.append(s0.elapsed_time(s1))
-    te = torch.tensor([statistics.mean(e2e_ms)], dtype=torch.float64, device=dev)
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = bits_per_step * world / (float(te.item()) * 1e-3) / 1e6
+    te = replicas.max_over_ranks(statistics.mean(e2e_ms), dev)
+    e2e_value = replicas.whole_job_rate(bits_per_step, world, te * 1e-3) / 1e6
+
+    extra = {}
+    if rank == 0 and not args.headline_only:
+        extra["uneven_256_blocks"] = measure_uneven(pa, inputs, torch, dev)
+        extra["serving"] = measure_serving(pa, inputs, torch, dev)
+        extra["long_block_2p27"] = measure_long_block(pa, inputs, torch, dev)
 
     if rank == 0:
         lat_sorted = sorted(lat_ms)
@@ -375,7 +472,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "n": list(N_VALUES), "m_over_n": list(RATIOS), "keys_per_batch": NKEYS,
                        "batches_per_step": len(cases), "mode": "FP32_GUARD", "transform_length": L,
                        "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas{world}"},
-            "latency_ms": {"p50": p50, "p99": p99, "unit": "ms per 64-key batch"},
+            "batch_latency_ms": {"p50": p50, "p99": p99, "unit": "ms per 64-key batch"},
             "fp64_plain": {"value": fp64_value, "unit": "Mbit/s",
                            "form": "single key per call, FP64 transforms, same (n, m) set"},
             "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -388,6 +485,11 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": "Mbit/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "clocks": clocks.summary(),
         }
+        if "serving" in extra:
+            sv = extra["serving"]
+            line["latency_ms"] = {"p50": sv["p50_ms"], "p99": sv["p99_ms"],
+                                  "unit": "ms per block, serving loop at 5000 blocks/s"}
+        line.update(extra)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line))
@@ -402,10 +504,11 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--headline-only", action="store_true", help="skip the uneven, serving and long-block legs")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
