@@ -47,6 +47,80 @@ __host__ __device__ constexpr double cos_pi16(int j) {
 __host__ __device__ constexpr double cos32(int j) { return j <= 8 ? cos_pi16(j) : -cos_pi16(16 - j); }
 __host__ __device__ constexpr double sin32(int j) { return j <= 8 ? cos_pi16(8 - j) : cos_pi16(j - 8); }
 
+// In-register DFT of RO = 3, 5 or 9 complex values (odd factors of smooth
+// transform lengths), natural order in and out. Forward roots w_R = exp(-2 pi i / R).
+// Constants: cos/sin of 2 pi j / R to 20 significant digits.
+template <typename T, bool INV>
+__device__ __forceinline__ void dft3(cx<T> &x0, cx<T> &x1, cx<T> &x2) {
+    constexpr T s3 = (T)0.86602540378443864676;  // sin(2 pi / 3)
+    const cx<T> a = Arith<T>::add(x1, x2), b = Arith<T>::sub(x1, x2);
+    const cx<T> c = Arith<T>::mk(x0.x - (T)0.5 * a.x, x0.y - (T)0.5 * a.y);
+    // forward: y1 = c - i s3 b, y2 = c + i s3 b (inverse swaps the signs)
+    const T sb_x = (INV ? -s3 : s3) * b.x, sb_y = (INV ? -s3 : s3) * b.y;
+    x0 = Arith<T>::add(x0, a);
+    x1 = Arith<T>::mk(c.x + sb_y, c.y - sb_x);
+    x2 = Arith<T>::mk(c.x - sb_y, c.y + sb_x);
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ void dft5(cx<T> *x) {
+    constexpr T c1 = (T)0.30901699437494742410, c2 = (T)-0.80901699437494742410;  // cos(2pi/5), cos(4pi/5)
+    constexpr T s1 = (T)0.95105651629515357212, s2 = (T)0.58778525229247312917;   // sin(2pi/5), sin(4pi/5)
+    const cx<T> a1 = Arith<T>::add(x[1], x[4]), b1 = Arith<T>::sub(x[1], x[4]);
+    const cx<T> a2 = Arith<T>::add(x[2], x[3]), b2 = Arith<T>::sub(x[2], x[3]);
+    const cx<T> x0 = x[0];
+    // real-coefficient parts
+    const cx<T> p1 = Arith<T>::mk(x0.x + c1 * a1.x + c2 * a2.x, x0.y + c1 * a1.y + c2 * a2.y);
+    const cx<T> p2 = Arith<T>::mk(x0.x + c2 * a1.x + c1 * a2.x, x0.y + c2 * a1.y + c1 * a2.y);
+    // q1 = s1 b1 + s2 b2, q2 = s2 b1 - s1 b2; y1 = p1 - i q1, y4 = p1 + i q1, y2 = p2 - i q2, y3 = p2 + i q2
+    T q1x = s1 * b1.x + s2 * b2.x, q1y = s1 * b1.y + s2 * b2.y;
+    T q2x = s2 * b1.x - s1 * b2.x, q2y = s2 * b1.y - s1 * b2.y;
+    if (INV) { q1x = -q1x; q1y = -q1y; q2x = -q2x; q2y = -q2y; }
+    x[0] = Arith<T>::add(x0, Arith<T>::add(a1, a2));
+    x[1] = Arith<T>::mk(p1.x + q1y, p1.y - q1x);
+    x[4] = Arith<T>::mk(p1.x - q1y, p1.y + q1x);
+    x[2] = Arith<T>::mk(p2.x + q2y, p2.y - q2x);
+    x[3] = Arith<T>::mk(p2.x - q2y, p2.y + q2x);
+}
+
+// x * w9^j for the radix-9 internal twiddles (j in 1, 2, 4).
+template <typename T, bool INV>
+__device__ __forceinline__ cx<T> rot9(cx<T> x, int j) {
+    const T c = j == 1 ? (T)0.76604444311897803520 : j == 2 ? (T)0.17364817766693034885 : (T)-0.93969262078590838405;
+    const T sn = j == 1 ? (T)0.64278760968653932632 : j == 2 ? (T)0.98480775301220805936 : (T)0.34202014332566873304;
+    const T s = INV ? sn : -sn;
+    return Arith<T>::mk(x.x * c - x.y * s, x.x * s + x.y * c);
+}
+
+template <typename T, int RO, bool INV>
+__device__ __forceinline__ void dft_odd(cx<T> *x) {
+    if constexpr (RO == 3) {
+        dft3<T, INV>(x[0], x[1], x[2]);
+    } else if constexpr (RO == 5) {
+        dft5<T, INV>(x);
+    } else {
+        static_assert(RO == 9, "odd radix must be 3, 5 or 9");
+        // 9 = 3 x 3: x[3m + r] -> DFT3 over m for each r, twiddle w9^{r k1}, DFT3 over r; X[k1 + 3 k2]
+        cx<T> a[9];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            cx<T> u0 = x[r], u1 = x[3 + r], u2 = x[6 + r];
+            dft3<T, INV>(u0, u1, u2);
+            a[3 * r + 0] = u0;  // k1 = 0
+            a[3 * r + 1] = r ? rot9<T, INV>(u1, r) : u1;
+            a[3 * r + 2] = r ? rot9<T, INV>(u2, 2 * r) : u2;
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < 3; ++k1) {
+            cx<T> v0 = a[k1], v1 = a[3 + k1], v2 = a[6 + k1];
+            dft3<T, INV>(v0, v1, v2);
+            x[k1] = v0;
+            x[k1 + 3] = v1;
+            x[k1 + 6] = v2;
+        }
+    }
+}
+
 // Twiddle table pair for the length-L transform root w_L: w_L^e = hi[e >> B] * lo[e & (2^B-1)].
 // Complex roots are exp(-2*pi*i/L), computed in double precision on the host and rounded to T.
 template <typename T> struct TwTab {
@@ -54,6 +128,10 @@ template <typename T> struct TwTab {
     const cx<T> *lo;
     uint32_t B;    // split position
     uint32_t lgL;  // log2 L
+    // In-CTA stage twiddles: fine[j] = w_F^j, where F (a divisor of L) is a
+    // multiple of every pass length of the plan.
+    const cx<T> *fine;
+    uint32_t F;
 };
 
 template <typename T> struct ComplexArith {
@@ -71,6 +149,11 @@ template <typename T> struct ComplexArith {
         const T s = INV ? (T)sin32(j) : -(T)sin32(j);
         return mk(x.x * c - x.y * s, x.x * s + x.y * c);
     }
+    template <bool INV> static __device__ __forceinline__ E fine(const TwTab<T> &t, uint32_t e) {
+        E w = __ldg(t.fine + e);
+        if (INV) w.y = -w.y;
+        return w;
+    }
     template <bool INV> static __device__ __forceinline__ E omega(const TwTab<T> &t, uint32_t e) {
         E a = __ldg(t.hi + (e >> t.B));
         E b = __ldg(t.lo + (e & ((1u << t.B) - 1u)));
@@ -79,7 +162,34 @@ template <typename T> struct ComplexArith {
         return w;
     }
 };
-template <> struct Arith<float> : ComplexArith<float> {};
+// FP32 complex add/sub as one packed f32x2 instruction each (sm_100+ packed FP32):
+// the (re, im) pair sits in one 64-bit register pair.
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) {
+    float2 d;
+    asm("{.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rd, ra, rb;\n\t"
+        "mov.b64 {%0, %1}, rd;}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
+    float2 d;
+    asm("{.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\t"
+        "mov.b64 {%0, %1}, rd;}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+template <> struct Arith<float> : ComplexArith<float> {
+    static __device__ __forceinline__ E add(E a, E b) { return f2_add(a, b); }
+    static __device__ __forceinline__ E sub(E a, E b) { return f2_sub(a, b); }
+};
 template <> struct Arith<double> : ComplexArith<double> {};
 
 }  // namespace pa
@@ -135,6 +245,18 @@ __device__ __forceinline__ void twiddle_chain(cx<T> *v, const TwTab<T> &tw, uint
     }
 }
 
+// v[r] *= w_F^{r*step} for r = 1..N-1 (one table load per value; the stage
+// twiddle w_{R p}^{r k} is w_F^{r k F/(R p)}).
+template <typename T, bool INV, int N>
+__device__ __forceinline__ void stage_twiddles(cx<T> *v, const TwTab<T> &tw, uint32_t step) {
+    uint32_t e = step;
+#pragma unroll
+    for (int r = 1; r < N; ++r) {
+        v[r] = Arith<T>::mul(v[r], Arith<T>::template fine<INV>(tw, e));
+        e += step;
+    }
+}
+
 // Shared-memory slot of element a of column col (COLS columns interleaved),
 // skewed by one slot every 16 to keep Stockham's strided writes conflict-free.
 template <int COLS>
@@ -149,18 +271,31 @@ constexpr uint32_t smem_elems() { return (uint32_t)LEN * COLS + ((uint32_t)LEN *
 // q stages; the forward transform uses radices [R0, E, ..., E], the inverse
 // [E, ..., E, R0], so the forward's output distribution over threads equals
 // the inverse's input distribution and the two chain in registers.
+__host__ __device__ constexpr int odd_part(int v) { return (v & 1) ? v : odd_part(v >> 1); }
+__host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+
+// Stage plan of a Stockham FFT of length LEN = RO * 2^k2 (RO odd: 1, 3, 5 or 9)
+// with E values per thread (TC = LEN / E threads per column). Radices:
+//   forward  [RO], R0, E, ..., E        inverse  E, ..., E, R0, [RO]
+// so the forward's output distribution over threads equals the inverse's input
+// distribution (the two chain in registers). An odd stage exists only in
+// transforms that read their input from, and write their output to, memory
+// (the innermost pass), because its E / RO groups per thread do not divide.
 template <int LEN, int E> struct Plan {
-    static constexpr int k = ilog2(LEN), e = ilog2(E);
-    static constexpr int q = (k + e - 1) / e;
+    static constexpr int RO = odd_part(LEN);
+    static constexpr int K2 = LEN / RO;
+    static constexpr int k = ilog2(K2), e = ilog2(E);
+    static constexpr int q = (k + e - 1) / e;  // power-of-two stages
     static constexpr int r0 = 1 << (k - (q - 1) * e);
     static constexpr int TC = LEN / E;  // threads per column
-    static_assert(q >= 2, "LEN must exceed E");
-    static_assert((1 << k) == LEN && (1 << e) == E, "powers of two only");
+    static_assert(RO == 1 || RO == 3 || RO == 5 || RO == 9, "odd factor must be 1, 3, 5 or 9");
+    static_assert(RO > 1 || q >= 2, "LEN must exceed E");
+    static_assert((1 << k) == K2 && (1 << e) == E && K2 >= E, "power-of-two part must be >= E");
 };
 
 // Index of the element that register slot s of thread tq holds at the start
 // (first-stage input) and at the end (last-stage output) of a transform.
-//   forward start / inverse end:  slot b*R0 + r  ->  tq + b*TC + r*(LEN/R0)
+//   forward start / inverse end:  slot b*R0 + r  ->  tq + b*TC + r*(LEN/R0)   (RO == 1)
 //   forward end / inverse start:  slot r         ->  tq + r*TC
 template <int LEN, int E>
 __device__ __forceinline__ uint32_t idx_r0(uint32_t tq, int s) {
@@ -172,24 +307,23 @@ __device__ __forceinline__ uint32_t idx_e(uint32_t tq, int s) {
     return tq + (uint32_t)s * (LEN / E);
 }
 
-// One Stockham stage of radix R at span p, from registers (already loaded
+// One Stockham stage of radix R at span P, from registers (already loaded
 // with this stage's inputs) to shared memory. Thread tq handles the E/R
 // butterfly groups i = tq + b*TC; group i reads elements i + r*LEN/R,
-// multiplies by w_{R p}^{r k} (k = i mod p), transforms, and writes element
-// (i - k)*R + k + r*p.
-template <typename T, int LEN, int COLS, int E, int R, bool INV>
-__device__ __forceinline__ void stage_to_smem(cx<T> *sm, cx<T> *v, uint32_t tq, uint32_t col, uint32_t p,
-                                              const TwTab<T> &tw) {
+// multiplies by w_{R P}^{r k} (k = i mod P; w_{R P}^{j} = w_F^{j F/(R P)}),
+// transforms, and writes element (i - k)*R + k + r*P.
+template <typename T, int LEN, int COLS, int E, int R, int P, bool INV>
+__device__ __forceinline__ void stage_to_smem(cx<T> *sm, cx<T> *v, uint32_t tq, uint32_t col, const TwTab<T> &tw) {
     constexpr int TC = LEN / E;
 #pragma unroll
     for (int b = 0; b < E / R; ++b) {
         const uint32_t i = tq + (uint32_t)b * TC;
-        const uint32_t k = i & (p - 1);
-        if (p > 1) twiddle_chain<T, INV, R>(v + b * R, tw, 0u, k << (tw.lgL - ilog2(R) - (31 - __clz(p))));
+        const uint32_t k = i % P;
+        if (P > 1) stage_twiddles<T, INV, R>(v + b * R, tw, k * (tw.F / (R * P)));
         dft<T, R, INV>(v + b * R);
         const uint32_t base = (i - k) * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) sm[sidx<COLS>(base + (uint32_t)r * p, col)] = v[b * R + r];
+        for (int r = 0; r < R; ++r) sm[sidx<COLS>(base + (uint32_t)r * P, col)] = v[b * R + r];
     }
 }
 
@@ -206,56 +340,120 @@ __device__ __forceinline__ void load_from_smem(const cx<T> *sm, cx<T> *v, uint32
 }
 
 // Last stage: twiddle + DFT in registers, results stay in registers.
-template <typename T, int LEN, int E, int R, bool INV>
-__device__ __forceinline__ void stage_in_regs(cx<T> *v, uint32_t tq, uint32_t p, const TwTab<T> &tw) {
+template <typename T, int LEN, int E, int R, int P, bool INV>
+__device__ __forceinline__ void stage_in_regs(cx<T> *v, uint32_t tq, const TwTab<T> &tw) {
     constexpr int TC = LEN / E;
 #pragma unroll
     for (int b = 0; b < E / R; ++b) {
         const uint32_t i = tq + (uint32_t)b * TC;
-        const uint32_t k = i & (p - 1);
-        if (p > 1) twiddle_chain<T, INV, R>(v + b * R, tw, 0u, k << (tw.lgL - ilog2(R) - (31 - __clz(p))));
+        const uint32_t k = i % P;
+        if (P > 1) stage_twiddles<T, INV, R>(v + b * R, tw, k * (tw.F / (R * P)));
         dft<T, R, INV>(v + b * R);
     }
 }
 
-// Full transform of length LEN on COLS interleaved columns. On entry v holds
-// the first-stage inputs (forward: idx_r0 layout; inverse: idx_e layout); on
-// exit v holds the outputs (forward: idx_e layout; inverse: idx_r0 layout).
-// The caller must __syncthreads() before the call if shared memory is still
-// being read from a previous transform.
+// Power-of-two stages S .. q-1 of the forward transform (radix R0 first, then
+// E), starting at span P0. Stage S's inputs are in registers when FROM_REGS,
+// else in shared memory. The last stage leaves its outputs in registers.
+template <typename T, int LEN, int COLS, int E, int S, int P0, bool FROM_REGS>
+__device__ __forceinline__ void fwd_pow2(cx<T> *sm, cx<T> *v, uint32_t tq, uint32_t col, const TwTab<T> &tw) {
+    using PL = Plan<LEN, E>;
+    constexpr int R = (S == 0) ? PL::r0 : E;
+    if constexpr (!FROM_REGS) {
+        __syncthreads();
+        load_from_smem<T, LEN, COLS, E, R>(sm, v, tq, col);
+    }
+    if constexpr (S == PL::q - 1) {
+        stage_in_regs<T, LEN, E, R, P0, false>(v, tq, tw);
+    } else {
+        if constexpr (!FROM_REGS) __syncthreads();
+        stage_to_smem<T, LEN, COLS, E, R, P0, false>(sm, v, tq, col, tw);
+        fwd_pow2<T, LEN, COLS, E, S + 1, P0 * R, false>(sm, v, tq, col, tw);
+    }
+}
+
+// Power-of-two stages of the inverse transform: E, ..., E, R0 (stage S counts
+// from the first). The first stage's inputs are in registers. With TO_SMEM the
+// last stage writes its outputs to shared memory (an odd stage follows),
+// otherwise they stay in registers.
+template <typename T, int LEN, int COLS, int E, int S, int P0, bool TO_SMEM>
+__device__ __forceinline__ void inv_pow2(cx<T> *sm, cx<T> *v, uint32_t tq, uint32_t col, const TwTab<T> &tw) {
+    using PL = Plan<LEN, E>;
+    constexpr int R = (S == PL::q - 1) ? PL::r0 : E;
+    if constexpr (S > 0) {
+        __syncthreads();
+        load_from_smem<T, LEN, COLS, E, R>(sm, v, tq, col);
+    }
+    if constexpr (S == PL::q - 1 && !TO_SMEM) {
+        stage_in_regs<T, LEN, E, R, P0, true>(v, tq, tw);
+    } else {
+        if constexpr (S > 0) __syncthreads();
+        stage_to_smem<T, LEN, COLS, E, R, P0, true>(sm, v, tq, col, tw);
+        if constexpr (S < PL::q - 1) inv_pow2<T, LEN, COLS, E, S + 1, P0 * R, TO_SMEM>(sm, v, tq, col, tw);
+    }
+}
+
+// Full power-of-two transform of length LEN on COLS interleaved columns. On
+// entry v holds the first-stage inputs (forward: idx_r0 layout; inverse:
+// idx_e layout); on exit v holds the outputs (forward: idx_e layout; inverse:
+// idx_r0 layout). The caller must __syncthreads() before the call if shared
+// memory is still being read from a previous transform.
 template <typename T, int LEN, int COLS, int E, bool INV>
 __device__ __forceinline__ void cta_fft(cx<T> *sm, cx<T> *v, uint32_t tq, uint32_t col, const TwTab<T> &tw) {
-    using P = Plan<LEN, E>;
-    // radix of stage s: forward [R0, E, ..., E], inverse [E, ..., E, R0]
-    uint32_t p = 1;
+    static_assert(Plan<LEN, E>::RO == 1, "odd lengths use cta_fft_fwd_odd / cta_fft_inv_odd");
     if constexpr (!INV) {
-        stage_to_smem<T, LEN, COLS, E, P::r0, INV>(sm, v, tq, col, p, tw);
-        p *= P::r0;
-#pragma unroll
-        for (int s = 1; s < P::q - 1; ++s) {
-            __syncthreads();
-            load_from_smem<T, LEN, COLS, E, E>(sm, v, tq, col);
-            __syncthreads();
-            stage_to_smem<T, LEN, COLS, E, E, INV>(sm, v, tq, col, p, tw);
-            p *= E;
-        }
-        __syncthreads();
-        load_from_smem<T, LEN, COLS, E, E>(sm, v, tq, col);
-        stage_in_regs<T, LEN, E, E, INV>(v, tq, p, tw);
+        fwd_pow2<T, LEN, COLS, E, 0, 1, true>(sm, v, tq, col, tw);
     } else {
-        stage_to_smem<T, LEN, COLS, E, E, INV>(sm, v, tq, col, p, tw);
-        p *= E;
+        inv_pow2<T, LEN, COLS, E, 0, 1, false>(sm, v, tq, col, tw);
+    }
+}
+
+// Forward transform of a contiguous row of LEN = RO * 2^k elements (RO > 1):
+// the odd first stage reads its inputs through ld(index) and writes shared
+// memory; the power-of-two stages follow. Outputs end in registers (idx_e).
+template <typename T, int LEN, int E, class Ld>
+__device__ __forceinline__ void cta_fft_fwd_odd(cx<T> *sm, cx<T> *v, uint32_t tq, const TwTab<T> &tw, Ld ld) {
+    using PL = Plan<LEN, E>;
+    constexpr int RO = PL::RO, K2 = PL::K2, TC = PL::TC;
+    constexpr int G = (K2 + TC - 1) / TC;  // odd groups per thread (the last may be partial)
 #pragma unroll
-        for (int s = 1; s < P::q - 1; ++s) {
-            __syncthreads();
-            load_from_smem<T, LEN, COLS, E, E>(sm, v, tq, col);
-            __syncthreads();
-            stage_to_smem<T, LEN, COLS, E, E, INV>(sm, v, tq, col, p, tw);
-            p *= E;
+    for (int j = 0; j < G; ++j) {
+        const uint32_t g = tq + (uint32_t)j * TC;
+        if (g < (uint32_t)K2) {
+            cx<T> u[RO];
+#pragma unroll
+            for (int r = 0; r < RO; ++r) u[r] = ld(g + (uint32_t)r * K2);
+            dft_odd<T, RO, false>(u);
+#pragma unroll
+            for (int r = 0; r < RO; ++r) sm[sidx<1>(g * RO + (uint32_t)r, 0)] = u[r];
         }
-        __syncthreads();
-        load_from_smem<T, LEN, COLS, E, P::r0>(sm, v, tq, col);
-        stage_in_regs<T, LEN, E, P::r0, INV>(v, tq, p, tw);
+    }
+    fwd_pow2<T, LEN, 1, E, 0, RO, false>(sm, v, tq, 0, tw);
+}
+
+// Inverse transform of a row (RO > 1): power-of-two stages from registers
+// (idx_e layout) into shared memory, then the odd last stage, whose outputs go
+// through st(index, value).
+template <typename T, int LEN, int E, class St>
+__device__ __forceinline__ void cta_fft_inv_odd(cx<T> *sm, cx<T> *v, uint32_t tq, const TwTab<T> &tw, St st) {
+    using PL = Plan<LEN, E>;
+    constexpr int RO = PL::RO, K2 = PL::K2, TC = PL::TC;
+    constexpr int G = (K2 + TC - 1) / TC;
+    inv_pow2<T, LEN, 1, E, 0, 1, true>(sm, v, tq, 0, tw);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+        const uint32_t g = tq + (uint32_t)j * TC;
+        if (g < (uint32_t)K2) {
+            cx<T> u[RO];
+#pragma unroll
+            for (int r = 0; r < RO; ++r) u[r] = sm[sidx<1>(g + (uint32_t)r * K2, 0)];
+            // span K2: twiddle w_LEN^{r g}
+            stage_twiddles<T, true, RO>(u, tw, g * (tw.F / LEN));
+            dft_odd<T, RO, true>(u);
+#pragma unroll
+            for (int r = 0; r < RO; ++r) st(g + (uint32_t)r * K2, u[r]);
+        }
     }
 }
 

@@ -53,48 +53,17 @@ struct DeviceGuard {
 
 inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-// Pass lengths (log2) for a complex transform of length 2^lgL. Two levels
-// while the innermost (contiguous) transform fits one CTA's shared memory,
-// three levels beyond.
-struct Shape3 {
-    int lg1, lg2, lg3;  // lg3 == 0: two levels, lg2 is the innermost
-};
-
-Shape3 choose_shape(int lgL, pa_dtype_t dtype) {
-    const int maxMid = dtype == PA_FP32_GUARD ? MaxLgMiddle<float>::v
-                       : dtype == PA_FP64     ? MaxLgMiddle<double>::v
-                                              : MaxLgMiddle<Zp>::v;
-    Shape3 s{0, 0, 0};
-    int lg1 = lgL - 12;
-    if (lg1 < kMinLgStrided) lg1 = kMinLgStrided;
-    if (lg1 > kMaxLgStrided) lg1 = kMaxLgStrided;
-    if (lgL - lg1 <= maxMid) {
-        s.lg1 = lg1;
-        s.lg2 = lgL - lg1;
-        return s;
-    }
-    // three levels: a short middle strided pass of 2^6, the rest split
-    const int lgm = kMinLgStrided;
-    int l1 = lgL - 12 - lgm;
-    if (l1 > kMaxLgStrided) l1 = kMaxLgStrided;
-    if (l1 < kMinLgStrided) l1 = kMinLgStrided;
-    s.lg1 = l1;
-    s.lg2 = lgm;
-    s.lg3 = lgL - l1 - lgm;
-    return s;
-}
-
 }  // namespace
 
 struct pa_plan {
     uint64_t n = 0, m = 0;
     pa_dtype_t dtype = PA_FP64;
     int device = 0;
-    int lgL = 0;
     uint64_t L = 0;
-    Shape3 shape{};
+    Geometry geo;  // pass split of L
     uint32_t twB = 0;
     void *tw_hi = nullptr, *tw_lo = nullptr;
+    void *tw_fine = nullptr;  // stage twiddles w_F^j, F = geo.F()
     void *spec = nullptr;        // L complex values, seed spectrum in digit-reversed order, times 1/L
     void *work = nullptr;        // work_pairs * L complex values
     uint32_t work_pairs = 0;
@@ -191,11 +160,13 @@ uint64_t zp_root(uint64_t L) {
 }
 
 template <typename T>
-int make_twiddles(int lgL, void **dhi, void **dlo, uint32_t *Bout) {
+int make_twiddles(uint64_t Lu, uint32_t F, void **dhi, void **dlo, uint32_t *Bout, void **dfine) {
+    int lgL = 0;
+    while ((1ull << lgL) < Lu) ++lgL;
     const uint32_t B = (uint32_t)(lgL + 1) / 2;
-    const uint64_t nhi = 1ull << (lgL - B), nlo = 1ull << B;
-    std::vector<cx<T>> hi(nhi), lo(nlo);
-    const double L = (double)(1ull << lgL);
+    const uint64_t nlo = 1ull << B, nhi = (Lu + nlo - 1) >> B;
+    std::vector<cx<T>> hi(nhi), lo(nlo), fine(F);
+    const double L = (double)Lu;
     const double two_pi = 6.283185307179586476925286766559;
     for (uint64_t h = 0; h < nhi; ++h) {
         const double a = two_pi * (double)(h << B) / L;
@@ -207,37 +178,52 @@ int make_twiddles(int lgL, void **dhi, void **dlo, uint32_t *Bout) {
         lo[l].x = (T)std::cos(a);
         lo[l].y = (T)-std::sin(a);
     }
+    for (uint64_t j = 0; j < F; ++j) {
+        const double a = two_pi * (double)j / (double)F;
+        fine[j].x = (T)std::cos(a);
+        fine[j].y = (T)-std::sin(a);
+    }
     PA_CUDA(cudaMalloc(dhi, nhi * sizeof(cx<T>)));
     PA_CUDA(cudaMalloc(dlo, nlo * sizeof(cx<T>)));
+    PA_CUDA(cudaMalloc(dfine, (size_t)F * sizeof(cx<T>)));
     PA_CUDA(cudaMemcpy(*dhi, hi.data(), nhi * sizeof(cx<T>), cudaMemcpyHostToDevice));
     PA_CUDA(cudaMemcpy(*dlo, lo.data(), nlo * sizeof(cx<T>), cudaMemcpyHostToDevice));
+    PA_CUDA(cudaMemcpy(*dfine, fine.data(), (size_t)F * sizeof(cx<T>), cudaMemcpyHostToDevice));
     *Bout = B;
     return PA_OK;
 }
 
 template <>
-int make_twiddles<Zp>(int lgL, void **dhi, void **dlo, uint32_t *Bout) {
+int make_twiddles<Zp>(uint64_t Lu, uint32_t F, void **dhi, void **dlo, uint32_t *Bout, void **dfine) {
+    if (Lu & (Lu - 1)) return PA_EUNSUPPORTED;  // the exact transform keeps power-of-two lengths
+    int lgL = 0;
+    while ((1ull << lgL) < Lu) ++lgL;
     const uint32_t B = (uint32_t)(lgL + 1) / 2;
     const uint64_t nhi = 1ull << (lgL - B), nlo = 1ull << B;
-    std::vector<uint64_t> hi(nhi), lo(nlo);
-    const uint64_t w = zp_root(1ull << lgL);
-    if (w == 0) return PA_EUNSUPPORTED;
+    std::vector<uint64_t> hi(nhi), lo(nlo), fine(F);
+    const uint64_t w = zp_root(Lu);
+    if (w == 0 || Lu % F) return PA_EUNSUPPORTED;
     const uint64_t wB = zp_pow_host(w, 1ull << B);
     uint64_t x = 1;
     for (uint64_t h = 0; h < nhi; ++h) { hi[h] = x; x = zp_mul_host(x, wB); }
     x = 1;
     for (uint64_t l = 0; l < nlo; ++l) { lo[l] = x; x = zp_mul_host(x, w); }
+    const uint64_t wF = zp_pow_host(w, Lu / F);  // w_F = w_L^(L/F): the same root system
+    x = 1;
+    for (uint64_t j = 0; j < F; ++j) { fine[j] = x; x = zp_mul_host(x, wF); }
     PA_CUDA(cudaMalloc(dhi, nhi * sizeof(uint64_t)));
     PA_CUDA(cudaMalloc(dlo, nlo * sizeof(uint64_t)));
+    PA_CUDA(cudaMalloc(dfine, (size_t)F * sizeof(uint64_t)));
     PA_CUDA(cudaMemcpy(*dhi, hi.data(), nhi * sizeof(uint64_t), cudaMemcpyHostToDevice));
     PA_CUDA(cudaMemcpy(*dlo, lo.data(), nlo * sizeof(uint64_t), cudaMemcpyHostToDevice));
+    PA_CUDA(cudaMemcpy(*dfine, fine.data(), (size_t)F * sizeof(uint64_t), cudaMemcpyHostToDevice));
     *Bout = B;
     return PA_OK;
 }
 
 template <typename T>
 int build_twiddles(pa_plan_t *p) {
-    return make_twiddles<T>(p->lgL, &p->tw_hi, &p->tw_lo, &p->twB);
+    return make_twiddles<T>(p->L, p->geo.F(), &p->tw_hi, &p->tw_lo, &p->twB, &p->tw_fine);
 }
 
 // 1/L as the element type's scaling factor.
@@ -256,7 +242,10 @@ TwTab<T> tw_of(const pa_plan_t *p) {
     t.hi = static_cast<const cx<T> *>(p->tw_hi);
     t.lo = static_cast<const cx<T> *>(p->tw_lo);
     t.B = p->twB;
-    t.lgL = (uint32_t)p->lgL;
+    t.lgL = 0;
+    while ((1ull << t.lgL) < p->L) ++t.lgL;  // log2 L for the power-of-two lengths of the exact transform
+    t.fine = static_cast<const cx<T> *>(p->tw_fine);
+    t.F = p->geo.F();
     return t;
 }
 
@@ -308,8 +297,8 @@ uint32_t chunk_pairs_limit(const pa_plan_t *p) {
     size_t per = (size_t)p->L * elem_bytes(p->dtype);
     size_t lim = budget / per;
     if (lim < 1) lim = 1;
-    if (p->shape.lg3) {
-        size_t nblk = p->L >> (p->shape.lg2 + p->shape.lg3);
+    if (p->geo.lgM) {
+        size_t nblk = (size_t)1 << p->geo.lg1;
         size_t y = 65535 / nblk;
         if (y < lim) lim = y;
     }
@@ -322,14 +311,13 @@ int run_seed(pa_plan_t *p, const uint64_t *seed, cudaStream_t st) {
     const TwTab<T> tw = tw_of<T>(p);
     cx<T> *W = static_cast<cx<T> *>(p->work);
     cx<T> *spec = static_cast<cx<T> *>(p->spec);
-    const Shape3 &s = p->shape;
-    { Timed t_(p, K_FWD_SEED, st); PA_CUDA(launch_fwd_seed<T>(s.lg1, seed, p->n, p->m, W, p->L, tw, st)); }
-    int inner = s.lg2;
-    if (s.lg3) {
-        { Timed t_(p, K_MID_FWD, st); PA_CUDA(launch_mid<T>(s.lg2, false, W, p->L, (uint32_t)s.lg3, 1, tw, st)); }
-        inner = s.lg3;
+    const Geometry &g = p->geo;
+    { Timed t_(p, K_FWD_SEED, st); PA_CUDA(launch_fwd_seed<T>(g.lg1, seed, p->n, p->m, W, p->L, tw, st)); }
+    if (g.lgM) {
+        Timed t_(p, K_MID_FWD, st);
+        PA_CUDA(launch_mid<T>(g.lgM, false, W, p->L, g.inner(), 1, tw, st));
     }
-    { Timed t_(p, K_MIDDLE_SPEC, st); PA_CUDA(launch_middle<T>(inner, 1, W, spec, p->L, 1, tw, inv_length<T>(p->L), st)); }
+    { Timed t_(p, K_MIDDLE_SPEC, st); PA_CUDA(launch_middle<T>(g.ro, g.lgI, 1, W, spec, p->L, 1, tw, inv_length<T>(p->L), st)); }
     return PA_OK;
 }
 
@@ -339,7 +327,7 @@ int run_keys(pa_plan_t *p, const uint64_t *keys, uint32_t nkeys, uint64_t kstrid
     const TwTab<T> tw = tw_of<T>(p);
     cx<T> *W = static_cast<cx<T> *>(p->work);
     cx<T> *spec = static_cast<cx<T> *>(p->spec);
-    const Shape3 &s = p->shape;
+    const Geometry &g = p->geo;
     { Timed t_(p, K_PREP, st); PA_CUDA(launch_prep(keys, nkeys, kstride, p->n, popc, marg, st)); }
     const uint32_t npairs = (nkeys + 1) / 2;
     for (uint32_t p0 = 0; p0 < npairs; p0 += p->work_pairs) {
@@ -348,15 +336,16 @@ int run_keys(pa_plan_t *p, const uint64_t *keys, uint32_t nkeys, uint64_t kstrid
         const uint32_t nk = (nkeys - k0 < 2 * pairs) ? nkeys - k0 : 2 * pairs;
         const uint64_t *kp = keys + (uint64_t)k0 * kstride;
         uint64_t *op = out + (uint64_t)k0 * ostride;
-        { Timed t_(p, K_FWD_KEYS, st); PA_CUDA(launch_fwd_keys<T>(s.lg1, kp, nk, kstride, p->n, W, p->L, pairs, tw, st)); }
-        if (s.lg3) {
-            { Timed t_(p, K_MID_FWD, st); PA_CUDA(launch_mid<T>(s.lg2, false, W, p->L, (uint32_t)s.lg3, pairs, tw, st)); }
-            { Timed t_(p, K_MIDDLE_CONV, st); PA_CUDA(launch_middle<T>(s.lg3, 0, W, spec, p->L, pairs, tw, one<T>(), st)); }
-            { Timed t_(p, K_MID_INV, st); PA_CUDA(launch_mid<T>(s.lg2, true, W, p->L, (uint32_t)s.lg3, pairs, tw, st)); }
+        { Timed t_(p, K_FWD_KEYS, st); PA_CUDA(launch_fwd_keys<T>(g.lg1, kp, nk, kstride, p->n, W, p->L, pairs, tw, st)); }
+        if (g.lgM) {
+            { Timed t_(p, K_MID_FWD, st); PA_CUDA(launch_mid<T>(g.lgM, false, W, p->L, g.inner(), pairs, tw, st)); }
+            { Timed t_(p, K_MIDDLE_CONV, st); PA_CUDA(launch_middle<T>(g.ro, g.lgI, 0, W, spec, p->L, pairs, tw, one<T>(), st)); }
+            { Timed t_(p, K_MID_INV, st); PA_CUDA(launch_mid<T>(g.lgM, true, W, p->L, g.inner(), pairs, tw, st)); }
         } else {
-            { Timed t_(p, K_MIDDLE_CONV, st); PA_CUDA(launch_middle<T>(s.lg2, 0, W, spec, p->L, pairs, tw, one<T>(), st)); }
+            Timed t_(p, K_MIDDLE_CONV, st);
+            PA_CUDA(launch_middle<T>(g.ro, g.lgI, 0, W, spec, p->L, pairs, tw, one<T>(), st));
         }
-        { Timed t_(p, K_INV_BITS, st); PA_CUDA(launch_inv_bits<T>(s.lg1, W, p->L, p->m, nk, popc + k0, marg + k0, op, ostride, pairs, tw, st)); }
+        { Timed t_(p, K_INV_BITS, st); PA_CUDA(launch_inv_bits<T>(g.lg1, W, p->L, p->m, nk, popc + k0, marg + k0, op, ostride, pairs, tw, st)); }
     }
     return PA_OK;
 }
@@ -366,6 +355,7 @@ void free_plan(pa_plan_t *p) {
     if (p->fallback) free_plan(p->fallback);
     cudaFree(p->tw_hi);
     cudaFree(p->tw_lo);
+    cudaFree(p->tw_fine);
     cudaFree(p->spec);
     cudaFree(p->work);
     cudaFree(p->popc);
@@ -379,10 +369,10 @@ void free_plan(pa_plan_t *p) {
 
 }  // namespace
 
-int pa_internal_twiddles(int lgL, int dtype, void **hi, void **lo, uint32_t *B) {
-    return dtype == PA_FP32_GUARD ? make_twiddles<float>(lgL, hi, lo, B)
-           : dtype == PA_FP64     ? make_twiddles<double>(lgL, hi, lo, B)
-                                  : make_twiddles<Zp>(lgL, hi, lo, B);
+int pa_internal_twiddles(uint64_t L, uint32_t F, int dtype, void **hi, void **lo, uint32_t *B, void **fine) {
+    return dtype == PA_FP32_GUARD ? make_twiddles<float>(L, F, hi, lo, B, fine)
+           : dtype == PA_FP64     ? make_twiddles<double>(L, F, hi, lo, B, fine)
+                                  : make_twiddles<Zp>(L, F, hi, lo, B, fine);
 }
 
 extern "C" {
@@ -419,15 +409,13 @@ int pa_plan(uint64_t n, uint64_t m, pa_dtype_t dtype, pa_plan_t **out) {
         return cuda_fail(cudaGetLastError(), "cudaGetDevice");
     }
     const uint64_t need = n + m - 1;
-    int lgL = 12;
-    while ((1ull << lgL) < need) ++lgL;
-    if (lgL > 28) {
+    const Geometry geo = choose_geometry(need, dtype, false);
+    if (geo.L == 0) {
         delete p;
         return PA_EUNSUPPORTED;
     }
-    p->lgL = lgL;
-    p->L = 1ull << lgL;
-    p->shape = choose_shape(lgL, dtype);
+    p->L = geo.L;
+    p->geo = geo;
     int rc = (dtype == PA_FP32_GUARD) ? build_twiddles<float>(p)
              : (dtype == PA_FP64)     ? build_twiddles<double>(p)
                                       : build_twiddles<Zp>(p);
@@ -460,9 +448,9 @@ int pa_plan_destroy(pa_plan_t *plan) {
 int pa_plan_shape(const pa_plan_t *p, uint64_t *L, uint32_t *L1, uint32_t *L2, uint32_t *L3) {
     if (!p) return PA_EINVAL;
     if (L) *L = p->L;
-    if (L1) *L1 = 1u << p->shape.lg1;
-    if (L2) *L2 = 1u << p->shape.lg2;
-    if (L3) *L3 = p->shape.lg3 ? (1u << p->shape.lg3) : 1u;
+    if (L1) *L1 = 1u << p->geo.lg1;
+    if (L2) *L2 = p->geo.lgM ? (1u << p->geo.lgM) : p->geo.inner();
+    if (L3) *L3 = p->geo.lgM ? p->geo.inner() : 1u;
     return PA_OK;
 }
 

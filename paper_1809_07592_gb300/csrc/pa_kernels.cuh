@@ -35,6 +35,9 @@ namespace pa {
 // threads, so the register allocation stays <= 64 per thread and at least two
 // CTAs overlap their load, transform and store phases.
 __host__ __device__ constexpr int min_blocks(int threads) { return threads >= 1024 ? 1 : (1024 / threads > 16 ? 16 : 1024 / threads); }
+// The fused innermost passes keep two transforms' worth of values live: ask for
+// 512 resident threads per SM (<= 128 registers each).
+__host__ __device__ constexpr int min_blocks_inner(int threads) { return threads >= 512 ? 1 : 512 / threads; }
 
 // Rounding to the nearest integer (ties to even) by adding and subtracting
 // 1.5 * 2^(mantissa bits): exact for |x| < 2^22 (float) / 2^51 (double); the
@@ -158,29 +161,28 @@ __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
 }
 
 // Middle-level strided pass (three-level plans only), forward or inverse.
-// Grid (S/COLS, blocks * pairs) with blocks = L / (LEN * S).
+// S is the innermost length (the stride of this pass); blocks of LEN*S elements;
+// w_{LEN*S}^e = w_L^{e * mult} with mult = L / (LEN*S). Grid (S/COLS, blocks * pairs).
 template <typename T, int LEN, int COLS, int E, bool INV>
 __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
-    k_mid(cx<T> *__restrict__ W, uint64_t L, uint32_t lgS, TwTab<T> tw) {
+    k_mid(cx<T> *__restrict__ W, uint64_t L, uint32_t S, uint32_t mult, TwTab<T> tw) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T> *sm = reinterpret_cast<cx<T> *>(smem_raw);
     const uint32_t col = threadIdx.x % COLS, tq = threadIdx.x / COLS;
-    const uint64_t S = 1ull << lgS;
-    const uint32_t lgBlk = ilog2(LEN) + lgS;
-    const uint64_t nblk = L >> lgBlk;
+    const uint64_t blk_len = (uint64_t)LEN * S;
+    const uint64_t nblk = L / blk_len;
     const uint64_t pair = blockIdx.y / nblk, blk = blockIdx.y % nblk;
     const uint32_t u = blockIdx.x * COLS + col;
-    const uint32_t sh = tw.lgL - lgBlk;  // w_{LEN*S}^{e} = w_L^{e << sh}
-    cx<T> *w = W + pair * L + (blk << lgBlk);
+    cx<T> *w = W + pair * L + blk * blk_len;
     cx<T> v[E];
 #pragma unroll
     for (int s = 0; s < E; ++s) {
         const uint32_t a = INV ? idx_e<LEN, E>(tq, s) : idx_r0<LEN, E>(tq, s);
         v[s] = w[(uint64_t)a * S + u];
     }
-    if (INV) twiddle_chain<T, true, E>(v, tw, (tq * u) << sh, ((LEN / E) * u) << sh);
+    if (INV) twiddle_chain<T, true, E>(v, tw, (tq * u) * mult, ((LEN / E) * u) * mult);
     cta_fft<T, LEN, COLS, E, INV>(sm, v, tq, col, tw);
-    if (!INV) twiddle_chain<T, false, E>(v, tw, (tq * u) << sh, ((LEN / E) * u) << sh);
+    if (!INV) twiddle_chain<T, false, E>(v, tw, (tq * u) * mult, ((LEN / E) * u) * mult);
 #pragma unroll
     for (int s = 0; s < E; ++s) {
         const uint32_t a = INV ? idx_r0<LEN, E>(tq, s) : idx_e<LEN, E>(tq, s);
@@ -192,7 +194,7 @@ __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
 // the seed spectrum, inverse (the fused convolution step). MODE 1: forward
 // only, scaled by 1/L, written as the seed spectrum.
 template <typename T, int LEN, int E, int MODE>
-__global__ void __launch_bounds__(LEN / E)
+__global__ void __launch_bounds__(LEN / E, min_blocks_inner(LEN / E))
     k_middle(cx<T> *__restrict__ W, cx<T> *__restrict__ spec, uint64_t L, TwTab<T> tw, cx<T> scale) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T> *sm = reinterpret_cast<cx<T> *>(smem_raw);
@@ -201,9 +203,13 @@ __global__ void __launch_bounds__(LEN / E)
     cx<T> *w = W + pair * L + row * LEN;
     cx<T> *sp = spec + row * LEN;
     cx<T> v[E];
+    if constexpr (Plan<LEN, E>::RO == 1) {
 #pragma unroll
-    for (int s = 0; s < E; ++s) v[s] = w[idx_r0<LEN, E>(tq, s)];
-    cta_fft<T, LEN, 1, E, false>(sm, v, tq, 0, tw);
+        for (int s = 0; s < E; ++s) v[s] = w[idx_r0<LEN, E>(tq, s)];
+        cta_fft<T, LEN, 1, E, false>(sm, v, tq, 0, tw);
+    } else {
+        cta_fft_fwd_odd<T, LEN, E>(sm, v, tq, tw, [&](uint32_t i) { return w[i]; });
+    }
     if (MODE == 1) {
 #pragma unroll
         for (int s = 0; s < E; ++s) sp[idx_e<LEN, E>(tq, s)] = Arith<T>::mul(v[s], scale);
@@ -212,9 +218,13 @@ __global__ void __launch_bounds__(LEN / E)
 #pragma unroll
     for (int s = 0; s < E; ++s) v[s] = Arith<T>::mul(v[s], sp[idx_e<LEN, E>(tq, s)]);
     __syncthreads();  // the forward transform's last shared-memory reads are done
-    cta_fft<T, LEN, 1, E, true>(sm, v, tq, 0, tw);
+    if constexpr (Plan<LEN, E>::RO == 1) {
+        cta_fft<T, LEN, 1, E, true>(sm, v, tq, 0, tw);
 #pragma unroll
-    for (int s = 0; s < E; ++s) w[idx_r0<LEN, E>(tq, s)] = v[s];
+        for (int s = 0; s < E; ++s) w[idx_r0<LEN, E>(tq, s)] = v[s];
+    } else {
+        cta_fft_inv_odd<T, LEN, E>(sm, v, tq, tw, [&](uint32_t i, cx<T> x) { w[i] = x; });
+    }
 }
 
 // Word type for COLS output bits.
@@ -356,7 +366,7 @@ __device__ __forceinline__ uint32_t split_row(uint32_t rho, uint32_t lgL1, uint3
 // Forward transform, Eq. 5-10 split with the mirror bin, X*V/L, then the
 // inverse transform of Y1 + i*Y2 written to the pair's slot in Wi.
 template <typename T, int LEN, int E>
-__global__ void __launch_bounds__(2 * (LEN / E))
+__global__ void __launch_bounds__(2 * (LEN / E), min_blocks_inner(2 * (LEN / E)))
     k_middle_split(const cx<T> *__restrict__ Wf, cx<T> *__restrict__ Wi, uint64_t L, uint32_t nblocks,
                    uint32_t lgL1, uint32_t lgM, TwTab<T> tw, T inv_L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -380,10 +390,14 @@ __global__ void __launch_bounds__(2 * (LEN / E))
     for (int which = 0; which < (has2 ? 2 : 1); ++which) {
         const cx<T> *w = Wf + (uint64_t)(which ? b2 : b1) * L + (uint64_t)row * LEN;
         cx<T> v[E];
-#pragma unroll
-        for (int s = 0; s < E; ++s) v[s] = w[idx_r0<LEN, E>(tq, s)];
         __syncthreads();  // previous use of the scratch is finished
-        cta_fft<T, LEN, 1, E, false>(sm, v, tq, 0, tw);
+        if constexpr (Plan<LEN, E>::RO == 1) {
+#pragma unroll
+            for (int s = 0; s < E; ++s) v[s] = w[idx_r0<LEN, E>(tq, s)];
+            cta_fft<T, LEN, 1, E, false>(sm, v, tq, 0, tw);
+        } else {
+            cta_fft_fwd_odd<T, LEN, E>(sm, v, tq, tw, [&](uint32_t i) { return w[i]; });
+        }
         __syncthreads();
 #pragma unroll
         for (int s = 0; s < E; ++s) sm[sidx<1>(idx_e<LEN, E>(tq, s), 0)] = v[s];
@@ -408,11 +422,18 @@ __global__ void __launch_bounds__(2 * (LEN / E))
         }
     }
     __syncthreads();
-    cta_fft<T, LEN, 1, E, true>(sm, y, tq, 0, tw);
-    if (self_paired && g == 1) return;
     cx<T> *wo = Wi + (uint64_t)blockIdx.y * L + (uint64_t)row * LEN;
+    const bool store = !(self_paired && g == 1);  // a self-paired row is written once
+    if constexpr (Plan<LEN, E>::RO == 1) {
+        cta_fft<T, LEN, 1, E, true>(sm, y, tq, 0, tw);
+        if (!store) return;
 #pragma unroll
-    for (int s = 0; s < E; ++s) wo[idx_r0<LEN, E>(tq, s)] = y[s];
+        for (int s = 0; s < E; ++s) wo[idx_r0<LEN, E>(tq, s)] = y[s];
+    } else {
+        cta_fft_inv_odd<T, LEN, E>(sm, y, tq, tw, [&](uint32_t i, cx<T> x) {
+            if (store) wo[i] = x;
+        });
+    }
 }
 
 // Level-1 inverse pass with bit output for pairs of blocks (real part: block

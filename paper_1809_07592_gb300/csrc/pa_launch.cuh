@@ -1,6 +1,8 @@
 // pa_launch.cuh -- launcher definitions; included by the per-type .cu files.
 #pragma once
 
+#include <type_traits>
+
 #include "pa_kernels.cuh"
 #include "pa_launch.h"
 
@@ -73,50 +75,90 @@ cudaError_t launch_fwd_seed(int lgLEN, const uint64_t *seed, uint64_t n, uint64_
 }
 
 template <typename T>
-cudaError_t launch_mid(int lgLEN, bool inverse, cx<T> *W, uint64_t L, uint32_t lgS, uint32_t pairs, TwTab<T> tw,
+cudaError_t launch_mid(int lgLEN, bool inverse, cx<T> *W, uint64_t L, uint32_t S, uint32_t pairs, TwTab<T> tw,
                        cudaStream_t st) {
     constexpr int E = Shape<T>::E, COLS = Shape<T>::COLS;
     return by_len<kMinLgStrided, kMinLgStrided>(lgLEN, [&](auto c) {
         constexpr int LEN = decltype(c)::value;
         constexpr size_t sb = smem_bytes<T, LEN, COLS>();
-        const uint64_t nblk = L >> (lgLEN + lgS);
-        dim3 grid((unsigned)((1ull << lgS) / COLS), (unsigned)(nblk * pairs));
+        const uint64_t nblk = L / ((uint64_t)LEN * S);
+        const uint32_t mult = (uint32_t)(L / ((uint64_t)LEN * S));
+        dim3 grid((unsigned)(S / COLS), (unsigned)(nblk * pairs));
         if (inverse) {
             auto kern = k_mid<T, LEN, COLS, E, true>;
             cudaError_t e = set_smem(kern, sb);
             if (e != cudaSuccess) return e;
-            kern<<<grid, COLS * LEN / E, sb, st>>>(W, L, lgS, tw);
+            kern<<<grid, COLS * LEN / E, sb, st>>>(W, L, S, mult, tw);
         } else {
             auto kern = k_mid<T, LEN, COLS, E, false>;
             cudaError_t e = set_smem(kern, sb);
             if (e != cudaSuccess) return e;
-            kern<<<grid, COLS * LEN / E, sb, st>>>(W, L, lgS, tw);
+            kern<<<grid, COLS * LEN / E, sb, st>>>(W, L, S, mult, tw);
         }
         return cudaGetLastError();
     });
 }
 
-template <typename T>
-cudaError_t launch_middle(int lgLEN, int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pairs, TwTab<T> tw,
-                          cx<T> scale, cudaStream_t st) {
+template <typename T, int LEN>
+cudaError_t middle_at(int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pairs, TwTab<T> tw, cx<T> scale,
+                      cudaStream_t st) {
     constexpr int E = Shape<T>::E;
-    return by_len<kMinLgMiddle, MaxLgMiddle<T>::v>(lgLEN, [&](auto c) {
-        constexpr int LEN = decltype(c)::value;
-        constexpr size_t sb = smem_bytes<T, LEN, 1>();
-        dim3 grid((unsigned)(L / LEN), pairs);
-        if (mode == 0) {
-            auto kern = k_middle<T, LEN, E, 0>;
-            cudaError_t e = set_smem(kern, sb);
-            if (e != cudaSuccess) return e;
-            kern<<<grid, LEN / E, sb, st>>>(W, spec, L, tw, scale);
-        } else {
-            auto kern = k_middle<T, LEN, E, 1>;
-            cudaError_t e = set_smem(kern, sb);
-            if (e != cudaSuccess) return e;
-            kern<<<grid, LEN / E, sb, st>>>(W, spec, L, tw, scale);
+    constexpr size_t sb = smem_bytes<T, LEN, 1>();
+    dim3 grid((unsigned)(L / LEN), pairs);
+    if (mode == 0) {
+        auto kern = k_middle<T, LEN, E, 0>;
+        cudaError_t e = set_smem(kern, sb);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, LEN / E, sb, st>>>(W, spec, L, tw, scale);
+    } else {
+        auto kern = k_middle<T, LEN, E, 1>;
+        cudaError_t e = set_smem(kern, sb);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, LEN / E, sb, st>>>(W, spec, L, tw, scale);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_middle(int ro, int lg, int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pairs, TwTab<T> tw,
+                          cx<T> scale, cudaStream_t st) {
+    if (ro == 1) {
+        return by_len<kMinLgMiddle, MaxLgMiddle<T>::v>(lg, [&](auto c) {
+            return middle_at<T, decltype(c)::value>(mode, W, spec, L, pairs, tw, scale, st);
+        });
+    }
+    if constexpr (std::is_same<T, Zp>::value) {
+        return cudaErrorInvalidValue;  // the exact transform keeps power-of-two lengths
+    } else {
+        if (ro == 3) return launch_middle_odd<T, 3>(lg, mode, W, spec, L, pairs, tw, scale, st);
+        if (ro == 5) return launch_middle_odd<T, 5>(lg, mode, W, spec, L, pairs, tw, scale, st);
+        if (ro == 9) return launch_middle_odd<T, 9>(lg, mode, W, spec, L, pairs, tw, scale, st);
+        return cudaErrorInvalidValue;
+    }
+}
+
+// Odd innermost lengths RO * 2^lg, lg in [kMinLgOdd, kMaxLgOdd], where the CTA fits.
+template <typename T, int RO, int LG = kMinLgOdd>
+cudaError_t odd_middle_dispatch(int lg, int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pairs, TwTab<T> tw,
+                                cx<T> scale, cudaStream_t st) {
+    if constexpr (LG > kMaxLgOdd) {
+        return cudaErrorInvalidValue;
+    } else {
+        if (lg == LG) {
+            if constexpr (odd_inner_ok<T>(RO, LG, false)) {
+                return middle_at<T, RO * (1 << LG)>(mode, W, spec, L, pairs, tw, scale, st);
+            } else {
+                return cudaErrorInvalidValue;
+            }
         }
-        return cudaGetLastError();
-    });
+        return odd_middle_dispatch<T, RO, LG + 1>(lg, mode, W, spec, L, pairs, tw, scale, st);
+    }
+}
+
+template <typename T, int RO>
+cudaError_t launch_middle_odd(int lg, int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pairs, TwTab<T> tw,
+                              cx<T> scale, cudaStream_t st) {
+    return odd_middle_dispatch<T, RO>(lg, mode, W, spec, L, pairs, tw, scale, st);
 }
 
 template <typename T>
@@ -143,7 +185,7 @@ cudaError_t launch_inv_bits(int lgLEN, const cx<T> *W, uint64_t L, uint64_t m, u
                                             TwTab<T>, cudaStream_t);                                             \
     template cudaError_t launch_mid<T>(int, bool, cx<T> *, uint64_t, uint32_t, uint32_t, TwTab<T>,               \
                                        cudaStream_t);                                                           \
-    template cudaError_t launch_middle<T>(int, int, cx<T> *, cx<T> *, uint64_t, uint32_t, TwTab<T>, cx<T>,       \
+    template cudaError_t launch_middle<T>(int, int, int, cx<T> *, cx<T> *, uint64_t, uint32_t, TwTab<T>, cx<T>,  \
                                           cudaStream_t);                                                        \
     template cudaError_t launch_inv_bits<T>(int, const cx<T> *, uint64_t, uint64_t, uint32_t, const uint32_t *,  \
                                             uint32_t *, uint64_t *, uint64_t, uint32_t, TwTab<T>, cudaStream_t);
@@ -164,21 +206,55 @@ cudaError_t launch_fwd_keyseed(int lgLEN, const BlockDev *blocks, uint32_t nbloc
     });
 }
 
-template <typename T>
-cudaError_t launch_middle_split(int lgLEN, const cx<T> *Wf, cx<T> *Wi, uint64_t L, uint32_t nblocks, uint32_t lgL1,
-                                uint32_t lgM, TwTab<T> tw, cudaStream_t st) {
+template <typename T, int LEN>
+cudaError_t split_at(const cx<T> *Wf, cx<T> *Wi, uint64_t L, uint32_t nblocks, uint32_t lgL1, uint32_t lgM,
+                     TwTab<T> tw, cudaStream_t st) {
     constexpr int E = Shape<T>::E;
-    return by_len<kMinLgMiddle, MaxLgSplit<T>::v>(lgLEN, [&](auto c) {
-        constexpr int LEN = decltype(c)::value;
-        auto kern = k_middle_split<T, LEN, E>;
-        constexpr size_t sb = 2 * smem_bytes<T, LEN, 1>();
-        cudaError_t e = set_smem(kern, sb);
-        if (e != cudaSuccess) return e;
-        const uint32_t R = (uint32_t)(L / LEN);
-        dim3 grid(R / 2 + 1, (nblocks + 1) / 2);
-        kern<<<grid, 2 * (LEN / E), sb, st>>>(Wf, Wi, L, nblocks, lgL1, lgM, tw, (T)(1.0 / (double)L));
-        return cudaGetLastError();
-    });
+    auto kern = k_middle_split<T, LEN, E>;
+    constexpr size_t sb = 2 * smem_bytes<T, LEN, 1>();
+    cudaError_t e = set_smem(kern, sb);
+    if (e != cudaSuccess) return e;
+    const uint32_t R = (uint32_t)(L / LEN);
+    dim3 grid(R / 2 + 1, (nblocks + 1) / 2);
+    kern<<<grid, 2 * (LEN / E), sb, st>>>(Wf, Wi, L, nblocks, lgL1, lgM, tw, (T)(1.0 / (double)L));
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_middle_split(int ro, int lg, const cx<T> *Wf, cx<T> *Wi, uint64_t L, uint32_t nblocks,
+                                uint32_t lgL1, uint32_t lgM, TwTab<T> tw, cudaStream_t st) {
+    if (ro == 1) {
+        return by_len<kMinLgMiddle, MaxLgSplit<T>::v>(lg, [&](auto c) {
+            return split_at<T, decltype(c)::value>(Wf, Wi, L, nblocks, lgL1, lgM, tw, st);
+        });
+    }
+    if (ro == 3) return launch_middle_split_odd<T, 3>(lg, Wf, Wi, L, nblocks, lgL1, lgM, tw, st);
+    if (ro == 5) return launch_middle_split_odd<T, 5>(lg, Wf, Wi, L, nblocks, lgL1, lgM, tw, st);
+    if (ro == 9) return launch_middle_split_odd<T, 9>(lg, Wf, Wi, L, nblocks, lgL1, lgM, tw, st);
+    return cudaErrorInvalidValue;
+}
+
+template <typename T, int RO, int LG = kMinLgOdd>
+cudaError_t odd_split_dispatch(int lg, const cx<T> *Wf, cx<T> *Wi, uint64_t L, uint32_t nblocks, uint32_t lgL1,
+                               uint32_t lgM, TwTab<T> tw, cudaStream_t st) {
+    if constexpr (LG > kMaxLgOdd) {
+        return cudaErrorInvalidValue;
+    } else {
+        if (lg == LG) {
+            if constexpr (odd_inner_ok<T>(RO, LG, true)) {
+                return split_at<T, RO * (1 << LG)>(Wf, Wi, L, nblocks, lgL1, lgM, tw, st);
+            } else {
+                return cudaErrorInvalidValue;
+            }
+        }
+        return odd_split_dispatch<T, RO, LG + 1>(lg, Wf, Wi, L, nblocks, lgL1, lgM, tw, st);
+    }
+}
+
+template <typename T, int RO>
+cudaError_t launch_middle_split_odd(int lg, const cx<T> *Wf, cx<T> *Wi, uint64_t L, uint32_t nblocks, uint32_t lgL1,
+                                    uint32_t lgM, TwTab<T> tw, cudaStream_t st) {
+    return odd_split_dispatch<T, RO>(lg, Wf, Wi, L, nblocks, lgL1, lgM, tw, st);
 }
 
 template <typename T>
@@ -200,9 +276,16 @@ cudaError_t launch_inv_bits_blocks(int lgLEN, const cx<T> *Wi, uint64_t L, const
 #define PA_INSTANTIATE_UNEVEN(T)                                                                                 \
     template cudaError_t launch_fwd_keyseed<T>(int, const BlockDev *, uint32_t, cx<T> *, uint64_t, TwTab<T>,     \
                                                cudaStream_t);                                                   \
-    template cudaError_t launch_middle_split<T>(int, const cx<T> *, cx<T> *, uint64_t, uint32_t, uint32_t,       \
+    template cudaError_t launch_middle_split<T>(int, int, const cx<T> *, cx<T> *, uint64_t, uint32_t, uint32_t,  \
                                                 uint32_t, TwTab<T>, cudaStream_t);                               \
     template cudaError_t launch_inv_bits_blocks<T>(int, const cx<T> *, uint64_t, const BlockDev *, uint32_t,     \
                                                    const uint32_t *, uint32_t *, TwTab<T>, cudaStream_t);
+
+// Odd innermost lengths of one (type, RO): the plain middle pass and the split pass.
+#define PA_INSTANTIATE_ODD(T, RO)                                                                               \
+    template cudaError_t launch_middle_odd<T, RO>(int, int, cx<T> *, cx<T> *, uint64_t, uint32_t, TwTab<T>,     \
+                                                  cx<T>, cudaStream_t);                                         \
+    template cudaError_t launch_middle_split_odd<T, RO>(int, const cx<T> *, cx<T> *, uint64_t, uint32_t,        \
+                                                        uint32_t, uint32_t, TwTab<T>, cudaStream_t);
 
 }  // namespace pa

@@ -1,9 +1,11 @@
 // pa_launch.h -- host-side launchers of the pass kernels (declarations).
 //
-// Each launcher picks the kernel instance for the pass length 2^lgLEN,
-// sets its dynamic shared memory and launches it on the given stream. The
-// definitions live in pa_launch.cuh and are instantiated once per arithmetic
-// type (pa_f32.cu for float, pa_f64.cu for double).
+// Each launcher picks the kernel instance for its pass length, sets its dynamic
+// shared memory and launches it on the given stream. Strided passes have
+// power-of-two lengths 2^lgLEN; innermost passes have lengths RO * 2^lg with an
+// odd factor RO in {1, 3, 5, 9} (smooth transform lengths). The definitions live
+// in pa_launch.cuh, instantiated per arithmetic type (pa_f32.cu, pa_f64.cu,
+// pa_zp.cu) and, for the odd innermost lengths, per (type, RO) (pa_*_r*.cu).
 #pragma once
 
 #include <cstdint>
@@ -38,12 +40,25 @@ cudaError_t launch_fwd_keys(int lgLEN, const uint64_t *keys, uint32_t nkeys, uin
 template <typename T>
 cudaError_t launch_fwd_seed(int lgLEN, const uint64_t *seed, uint64_t n, uint64_t m, cx<T> *W, uint64_t L,
                             TwTab<T> tw, cudaStream_t st);
+// S: innermost length (the stride of the middle strided pass).
 template <typename T>
-cudaError_t launch_mid(int lgLEN, bool inverse, cx<T> *W, uint64_t L, uint32_t lgS, uint32_t pairs, TwTab<T> tw,
+cudaError_t launch_mid(int lgLEN, bool inverse, cx<T> *W, uint64_t L, uint32_t S, uint32_t pairs, TwTab<T> tw,
                        cudaStream_t st);
+// Innermost pass of length ro * 2^lg.
 template <typename T>
-cudaError_t launch_middle(int lgLEN, int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pairs, TwTab<T> tw,
+cudaError_t launch_middle(int ro, int lg, int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pairs, TwTab<T> tw,
                           cx<T> scale, cudaStream_t st);
+template <typename T, int RO>
+cudaError_t launch_middle_odd(int lg, int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pairs, TwTab<T> tw,
+                              cx<T> scale, cudaStream_t st);
+
+// Limits of the odd innermost lengths RO * 2^lg: a CTA has RO * 2^lg / E threads
+// (at most 1024, or 512 per row for the two-row split kernel).
+constexpr int kMinLgOdd = 7, kMaxLgOdd = 11;
+template <typename T>
+constexpr bool odd_inner_ok(int ro, int lg, bool split) {
+    return lg >= kMinLgOdd && lg <= kMaxLgOdd && (long long)ro * (1ll << lg) / Shape<T>::E <= (split ? 512 : 1024);
+}
 template <typename T>
 cudaError_t launch_inv_bits(int lgLEN, const cx<T> *W, uint64_t L, uint64_t m, uint32_t nkeys,
                             const uint32_t *popc, uint32_t *margin_bits, uint64_t *out, uint64_t ostride,
@@ -61,8 +76,11 @@ template <typename T>
 cudaError_t launch_fwd_keyseed(int lgLEN, const BlockDev *blocks, uint32_t nblocks, cx<T> *W, uint64_t L,
                                TwTab<T> tw, cudaStream_t st);
 template <typename T>
-cudaError_t launch_middle_split(int lgLEN, const cx<T> *Wf, cx<T> *Wi, uint64_t L, uint32_t nblocks, uint32_t lgL1,
-                                uint32_t lgM, TwTab<T> tw, cudaStream_t st);
+cudaError_t launch_middle_split(int ro, int lg, const cx<T> *Wf, cx<T> *Wi, uint64_t L, uint32_t nblocks,
+                                uint32_t lgL1, uint32_t lgM, TwTab<T> tw, cudaStream_t st);
+template <typename T, int RO>
+cudaError_t launch_middle_split_odd(int lg, const cx<T> *Wf, cx<T> *Wi, uint64_t L, uint32_t nblocks, uint32_t lgL1,
+                                    uint32_t lgM, TwTab<T> tw, cudaStream_t st);
 template <typename T>
 cudaError_t launch_inv_bits_blocks(int lgLEN, const cx<T> *Wi, uint64_t L, const BlockDev *blocks, uint32_t nblocks,
                                    const uint32_t *popc, uint32_t *margin_bits, TwTab<T> tw, cudaStream_t st);

@@ -31,7 +31,6 @@
 
 using namespace pa;
 using pa::blocks::ClassRun;
-using pa::blocks::Split;
 
 namespace {
 
@@ -44,7 +43,7 @@ uint64_t now_ns() {
 struct Request {
     uint64_t ticket = 0;
     pa_block_desc_t d{};
-    int lgL = 0;
+    uint64_t L = 0;  // transform length of the block's class
     size_t bytes = 0;
     uint64_t t_submit = 0, t_admit = 0;
 };
@@ -62,7 +61,7 @@ struct Slot {  // one stream and its in-flight micro-batch
 };
 
 struct Twiddles {
-    void *hi = nullptr, *lo = nullptr;
+    void *hi = nullptr, *lo = nullptr, *fine = nullptr;
     uint32_t B = 0;
 };
 
@@ -88,23 +87,24 @@ struct pa_server {
     std::vector<Slot> slots;
     size_t next_slot = 0;
     cudaMemPool_t pool = nullptr;
-    std::map<int, Twiddles> tw;
+    std::map<std::pair<uint64_t, uint32_t>, Twiddles> tw;  // by (L, F)
     std::map<std::pair<uint64_t, uint64_t>, pa_plan_t *> esc;
     cudaStream_t esc_stream = nullptr;
 };
 
 namespace {
 
-int twiddles_for(pa_server_t *s, int lgL, Twiddles *out) {
-    auto it = s->tw.find(lgL);
+int twiddles_for(pa_server_t *s, const Geometry &g, Twiddles *out) {
+    const auto key = std::make_pair(g.L, g.F());
+    auto it = s->tw.find(key);
     if (it != s->tw.end()) {
         *out = it->second;
         return PA_OK;
     }
     Twiddles t;
-    int rc = pa_internal_twiddles(lgL, (int)s->cfg.dtype, &t.hi, &t.lo, &t.B);
+    int rc = pa_internal_twiddles(g.L, g.F(), (int)s->cfg.dtype, &t.hi, &t.lo, &t.B, &t.fine);
     if (rc != PA_OK) return rc;
-    s->tw[lgL] = t;
+    s->tw[key] = t;
     *out = t;
     return PA_OK;
 }
@@ -113,15 +113,15 @@ int twiddles_for(pa_server_t *s, int lgL, Twiddles *out) {
 int launch_batch(pa_server_t *s, Slot &sl) {
     const uint32_t nb = (uint32_t)sl.reqs.size();
     const size_t esz = s->cfg.dtype == PA_FP32_GUARD ? sizeof(float2) : sizeof(double2);
-    std::map<int, std::vector<uint32_t>> byL;
-    for (uint32_t i = 0; i < nb; ++i) byL[sl.reqs[i].lgL].push_back(i);
+    std::map<uint64_t, std::vector<uint32_t>> byL;
+    for (uint32_t i = 0; i < nb; ++i) byL[sl.reqs[i].L].push_back(i);
     // one pool allocation per micro-batch: counters, descriptors, then per-class work slots
     size_t off_cnt = 0;
     size_t off_desc = align256(2 * (size_t)nb * sizeof(uint32_t));
     size_t total = off_desc + align256((size_t)nb * sizeof(BlockDev));
     std::vector<std::pair<size_t, size_t>> work_off;  // (Wf, Wi) offsets per class
     for (auto &kv : byL) {
-        const size_t L = (size_t)1 << kv.first;
+        const size_t L = (size_t)kv.first;
         const size_t k = kv.second.size();
         const size_t wf = total;
         total += align256(k * L * esz);
@@ -151,13 +151,11 @@ int launch_batch(pa_server_t *s, Slot &sl) {
     size_t ci = 0;
     for (auto &kv : byL) {
         if (rc != PA_OK) break;
-        Twiddles t;
-        rc = twiddles_for(s, kv.first, &t);
-        if (rc != PA_OK) break;
         ClassRun c;
-        c.lgL = kv.first;
-        c.L = 1ull << kv.first;
-        if (!pa::blocks::cached_split(kv.first, s->cfg.dtype, &c.sp)) c.sp = pa::blocks::default_split(kv.first, s->cfg.dtype);
+        if (!pa::blocks::cached_split(kv.first, s->cfg.dtype, &c.geo)) c.geo = pa::blocks::default_split(kv.first, s->cfg.dtype);
+        Twiddles t;
+        rc = twiddles_for(s, c.geo, &t);
+        if (rc != PA_OK) break;
         c.d_blocks = d_desc + class_first[ci];
         c.nb = (uint32_t)kv.second.size();
         c.Wf = mem + work_off[ci].first;
@@ -165,6 +163,7 @@ int launch_batch(pa_server_t *s, Slot &sl) {
         c.tw_hi = t.hi;
         c.tw_lo = t.lo;
         c.B = t.B;
+        c.tw_fine = t.fine;
         rc = pa::blocks::run_complex(s->cfg.dtype, c, popc, marg, sl.st);
         ++ci;
     }
@@ -315,6 +314,7 @@ void free_server(pa_server_t *s) {
     for (auto &kv : s->tw) {
         cudaFree(kv.second.hi);
         cudaFree(kv.second.lo);
+        cudaFree(kv.second.fine);
     }
     for (auto &kv : s->esc) pa_plan_destroy(kv.second);
     if (s->esc_stream) cudaStreamDestroy(s->esc_stream);
@@ -380,9 +380,9 @@ int pa_submit(pa_server_t *s, const pa_block_desc_t *b, uint64_t *ticket) {
         return PA_EINVAL;
     Request r;
     r.d = *b;
-    r.lgL = pa::blocks::lg_length(b->n, b->m);
-    if (r.lgL > 28) return PA_EUNSUPPORTED;
-    r.bytes = pa::blocks::scratch_per_block(r.lgL, s->cfg.dtype);
+    r.L = pa::blocks::class_length(b->n, b->m, s->cfg.dtype);
+    if (r.L == 0) return PA_EUNSUPPORTED;
+    r.bytes = pa::blocks::scratch_per_block(r.L, s->cfg.dtype);
     if (r.bytes > s->cfg.hbm_cap_bytes) return PA_EINVAL;  // could never be admitted
     r.t_submit = now_ns();
     {

@@ -52,34 +52,43 @@ int scratch_address(unsigned char **out) {
     return PA_OK;
 }
 
-// w_L^e for the complex transforms: exp(-2 pi i e / L) in double precision.
+// Twiddles of the complex transforms, exp(-2 pi i e / L) in double precision:
+// the two-level table (hi, lo) and the stage table fine[j] = w_F^j, F = 2^lgF.
 template <typename T>
-__global__ void k_twiddles_complex(cx<T> *hi, cx<T> *lo, uint32_t B, uint32_t lgL) {
-    const uint32_t nhi = 1u << (lgL - B), nlo = 1u << B;
+__global__ void k_twiddles_complex(cx<T> *hi, cx<T> *lo, uint32_t B, uint32_t lgL, cx<T> *fine, uint32_t lgF) {
+    const uint32_t nhi = 1u << (lgL - B), nlo = 1u << B, nf = 1u << lgF;
     const double inv = 1.0 / (double)(1ull << lgL);
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nhi + nlo; i += gridDim.x * blockDim.x) {
-        const uint64_t e = i < nhi ? ((uint64_t)i << B) : (uint64_t)(i - nhi);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nhi + nlo + nf; i += gridDim.x * blockDim.x) {
         double s, c;
-        sincospi(2.0 * (double)e * inv, &s, &c);
+        if (i < nhi + nlo) {
+            const uint64_t e = i < nhi ? ((uint64_t)i << B) : (uint64_t)(i - nhi);
+            sincospi(2.0 * (double)e * inv, &s, &c);
+        } else {
+            sincospi(2.0 * (double)(i - nhi - nlo) / (double)nf, &s, &c);
+        }
         cx<T> w;
         w.x = (T)c;
         w.y = (T)-s;
-        if (i < nhi) hi[i] = w; else lo[i - nhi] = w;
+        if (i < nhi) hi[i] = w; else if (i < nhi + nlo) lo[i - nhi] = w; else fine[i - nhi - nlo] = w;
     }
 }
 
-// w_L^e modulo p for the exact transform, by square-and-multiply from the root w.
-__global__ void k_twiddles_zp(uint64_t *hi, uint64_t *lo, uint32_t B, uint32_t lgL, uint64_t w) {
-    const uint32_t nhi = 1u << (lgL - B), nlo = 1u << B;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nhi + nlo; i += gridDim.x * blockDim.x) {
-        uint64_t e = i < nhi ? ((uint64_t)i << B) : (uint64_t)(i - nhi);
+// w_L^e modulo p for the exact transform, by square-and-multiply from the root w;
+// the stage table holds w_F^j = w_L^(j L/F).
+__global__ void k_twiddles_zp(uint64_t *hi, uint64_t *lo, uint32_t B, uint32_t lgL, uint64_t w, uint64_t *fine,
+                              uint32_t lgF) {
+    const uint32_t nhi = 1u << (lgL - B), nlo = 1u << B, nf = 1u << lgF;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nhi + nlo + nf; i += gridDim.x * blockDim.x) {
+        uint64_t e = i < nhi ? ((uint64_t)i << B)
+                     : i < nhi + nlo ? (uint64_t)(i - nhi)
+                                     : ((uint64_t)(i - nhi - nlo) << (lgL - lgF));
         uint64_t r = 1, b = w;
         while (e) {
             if (e & 1) r = zp_mul(r, b);
             b = zp_mul(b, b);
             e >>= 1;
         }
-        if (i < nhi) hi[i] = r; else lo[i - nhi] = r;
+        if (i < nhi) hi[i] = r; else if (i < nhi + nlo) lo[i - nhi] = r; else fine[i - nhi - nlo] = r;
     }
 }
 
@@ -130,15 +139,21 @@ int run_static(unsigned char *base, int lgL, uint64_t n, uint64_t m, const uint6
     const uint32_t B = (uint32_t)(lgL + 1) / 2;
     cx<T> *hi = reinterpret_cast<cx<T> *>(tail);
     cx<T> *lo = hi + (1u << (lgL - B));
+    int lg1 = lgL - 12;
+    if (lg1 < kMinLgStrided) lg1 = kMinLgStrided;
+    if (lg1 > kMaxLgStrided) lg1 = kMaxLgStrided;
+    const int lg2 = lgL - lg1;  // <= 12 for lgL <= 21: always a two-level split
+    const uint32_t lgF = (uint32_t)(lg1 > lg2 ? lg1 : lg2);  // stage table: lcm of the pass lengths
+    cx<T> *fine = reinterpret_cast<cx<T> *>(tail + (64u << 10));  // after hi/lo (<= 48 KiB); <= 64 KiB
     uint32_t *popc = reinterpret_cast<uint32_t *>(tail + (512u << 10));
     uint32_t *marg = popc + 2;
     if constexpr (std::is_same<T, Zp>::value) {
         const uint64_t w = root_of_order(L);
         if (!w) return PA_EUNSUPPORTED;
         k_twiddles_zp<<<64, 256, 0, st>>>(reinterpret_cast<uint64_t *>(hi), reinterpret_cast<uint64_t *>(lo), B,
-                                          (uint32_t)lgL, w);
+                                          (uint32_t)lgL, w, reinterpret_cast<uint64_t *>(fine), lgF);
     } else {
-        k_twiddles_complex<T><<<64, 256, 0, st>>>(hi, lo, B, (uint32_t)lgL);
+        k_twiddles_complex<T><<<64, 256, 0, st>>>(hi, lo, B, (uint32_t)lgL, fine, lgF);
     }
     STATIC_CUDA(cudaGetLastError());
     TwTab<T> tw;
@@ -146,15 +161,13 @@ int run_static(unsigned char *base, int lgL, uint64_t n, uint64_t m, const uint6
     tw.lo = lo;
     tw.B = B;
     tw.lgL = (uint32_t)lgL;
-    int lg1 = lgL - 12;
-    if (lg1 < kMinLgStrided) lg1 = kMinLgStrided;
-    if (lg1 > kMaxLgStrided) lg1 = kMaxLgStrided;
-    const int lg2 = lgL - lg1;  // <= 12 for lgL <= 21: always a two-level split
+    tw.fine = fine;
+    tw.F = 1u << lgF;
     STATIC_CUDA(launch_fwd_seed<T>(lg1, seed, n, m, W, L, tw, st));
-    STATIC_CUDA(launch_middle<T>(lg2, 1, W, spec, L, 1, tw, scale_of<T>(L), st));
+    STATIC_CUDA(launch_middle<T>(1, lg2, 1, W, spec, L, 1, tw, scale_of<T>(L), st));
     STATIC_CUDA(launch_prep(keys, nkeys, kstride, n, popc, marg, st));  // also zeroes the margins
     STATIC_CUDA(launch_fwd_keys<T>(lg1, keys, nkeys, kstride, n, W, L, 1, tw, st));
-    STATIC_CUDA(launch_middle<T>(lg2, 0, W, spec, L, 1, tw, unit<T>(), st));
+    STATIC_CUDA(launch_middle<T>(1, lg2, 0, W, spec, L, 1, tw, unit<T>(), st));
     STATIC_CUDA(launch_inv_bits<T>(lg1, W, L, m, nkeys, popc, marg, out, ostride, 1, tw, st));
     return PA_OK;
 }

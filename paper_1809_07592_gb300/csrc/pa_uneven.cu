@@ -24,7 +24,6 @@
 
 using namespace pa;
 using pa::blocks::ClassRun;
-using pa::blocks::Split;
 
 namespace {
 
@@ -35,22 +34,20 @@ namespace {
     } while (0)
 
 struct UClass {
-    int lgL = 0;
-    uint64_t L = 0;
-    Split sp;
+    Geometry geo;                    // length L and the chosen split
     std::vector<uint32_t> ids;       // caller indices of the blocks in this class
     BlockDev *d_blocks = nullptr;    // device descriptors
     void *Wf = nullptr, *Wi = nullptr;  // forward slots (one per block), inverse slots (one per pair)
     void *spec = nullptr;            // NTT mode: one seed-spectrum slot, blocks run one after another
     void *tw_hi = nullptr, *tw_lo = nullptr;
     uint32_t B = 0;
+    void *tw_fine = nullptr;         // stage twiddles, length geo.F() (rebuilt when the split changes F)
+    uint32_t fineF = 0;
     cudaStream_t st = nullptr;
     cudaEvent_t done = nullptr;
-    ClassRun run(const Split &s) const {
+    ClassRun run(const Geometry &g) const {
         ClassRun r;
-        r.lgL = lgL;
-        r.L = L;
-        r.sp = s;
+        r.geo = g;
         r.d_blocks = d_blocks;
         r.nb = (uint32_t)ids.size();
         r.Wf = Wf;
@@ -59,14 +56,15 @@ struct UClass {
         r.tw_hi = tw_hi;
         r.tw_lo = tw_lo;
         r.B = B;
+        r.tw_fine = tw_fine;
         return r;
     }
 };
 
 // ---------------------------------------------------------------------------
-// Autotuner cache: best split per (lgL, dtype), measured on the first batch that needs it.
+// Autotuner cache: best split per (L, dtype), measured on the first batch that needs it.
 std::mutex g_tune_mu;
-std::map<std::pair<int, int>, Split> g_tune;
+std::map<std::pair<uint64_t, int>, Geometry> g_tune;
 bool g_tune_loaded = false;
 
 void tune_load_locked() {
@@ -76,14 +74,11 @@ void tune_load_locked() {
     if (!path) return;
     FILE *f = std::fopen(path, "r");
     if (!f) return;
-    int lgL, dt, a, b, c;
-    while (std::fscanf(f, "%d %d %d %d %d", &lgL, &dt, &a, &b, &c) == 5) g_tune[{lgL, dt}] = Split{a, b, c};
+    unsigned long long L;
+    int dt, a, b, ro, lgI;
+    while (std::fscanf(f, "%llu %d %d %d %d %d", &L, &dt, &a, &b, &ro, &lgI) == 6)
+        g_tune[{(uint64_t)L, dt}] = Geometry{(uint64_t)L, a, b, ro, lgI};
     std::fclose(f);
-}
-
-int max_inner(pa_dtype_t dtype) {
-    return dtype == PA_FP32_GUARD ? MaxLgSplit<float>::v : dtype == PA_FP64 ? MaxLgSplit<double>::v
-                                                                              : MaxLgMiddle<Zp>::v;
 }
 
 }  // namespace
@@ -114,19 +109,22 @@ TwTab<T> tw_of(const ClassRun &c) {
     t.hi = static_cast<const cx<T> *>(c.tw_hi);
     t.lo = static_cast<const cx<T> *>(c.tw_lo);
     t.B = c.B;
-    t.lgL = (uint32_t)c.lgL;
+    t.lgL = 0;
+    while ((1ull << t.lgL) < c.geo.L) ++t.lgL;
+    t.fine = static_cast<const cx<T> *>(c.tw_fine);
+    t.F = c.geo.F();
     return t;
 }
 
 // Middle strided pass over `slots` consecutive slots, chunked to the grid's y limit.
 template <typename T>
 int mid_chunks(const ClassRun &c, bool inverse, cx<T> *W, uint32_t slots, cudaStream_t st) {
-    const uint32_t nblk = (uint32_t)(c.L >> (c.sp.lgM + c.sp.lgI));
+    const uint32_t nblk = 1u << c.geo.lg1;
     const uint32_t per = 65535u / nblk;
     const TwTab<T> tw = tw_of<T>(c);
     for (uint32_t s0 = 0; s0 < slots; s0 += per) {
         const uint32_t k = (slots - s0 < per) ? slots - s0 : per;
-        U_CUDA(launch_mid<T>(c.sp.lgM, inverse, W + (uint64_t)s0 * c.L, c.L, (uint32_t)c.sp.lgI, k, tw, st));
+        U_CUDA(launch_mid<T>(c.geo.lgM, inverse, W + (uint64_t)s0 * c.geo.L, c.geo.L, c.geo.inner(), k, tw, st));
     }
     return PA_OK;
 }
@@ -134,22 +132,22 @@ int mid_chunks(const ClassRun &c, bool inverse, cx<T> *W, uint32_t slots, cudaSt
 // The whole chain of one class (complex modes).
 template <typename T>
 int run_class_complex(const ClassRun &c, uint32_t *popc, uint32_t *marg, cudaStream_t st) {
-    const Split &sp = c.sp;
+    const Geometry &g = c.geo;
     const uint32_t nb = c.nb;
     const TwTab<T> tw = tw_of<T>(c);
     cx<T> *Wf = static_cast<cx<T> *>(c.Wf), *Wi = static_cast<cx<T> *>(c.Wi);
     U_CUDA(launch_prep_blocks(c.d_blocks, nb, popc, marg, st));
-    U_CUDA(launch_fwd_keyseed<T>(sp.lg1, c.d_blocks, nb, Wf, c.L, tw, st));
-    if (sp.lgM) {
+    U_CUDA(launch_fwd_keyseed<T>(g.lg1, c.d_blocks, nb, Wf, g.L, tw, st));
+    if (g.lgM) {
         int rc = mid_chunks<T>(c, false, Wf, nb, st);
         if (rc != PA_OK) return rc;
     }
-    U_CUDA(launch_middle_split<T>(sp.lgI, Wf, Wi, c.L, nb, (uint32_t)sp.lg1, (uint32_t)sp.lgM, tw, st));
-    if (sp.lgM) {
+    U_CUDA(launch_middle_split<T>(g.ro, g.lgI, Wf, Wi, g.L, nb, (uint32_t)g.lg1, (uint32_t)g.lgM, tw, st));
+    if (g.lgM) {
         int rc = mid_chunks<T>(c, true, Wi, (nb + 1) / 2, st);
         if (rc != PA_OK) return rc;
     }
-    U_CUDA(launch_inv_bits_blocks<T>(sp.lg1, Wi, c.L, c.d_blocks, nb, popc, marg, tw, st));
+    U_CUDA(launch_inv_bits_blocks<T>(g.lg1, Wi, g.L, c.d_blocks, nb, popc, marg, tw, st));
     return PA_OK;
 }
 
@@ -158,51 +156,71 @@ int run_class_ntt(const ClassRun &c, const pa_block_desc_t *hb, const uint32_t *
                   uint32_t *marg, cudaStream_t st) {
     const TwTab<Zp> tw = tw_of<Zp>(c);
     cx<Zp> *W = static_cast<cx<Zp> *>(c.Wf), *spec = static_cast<cx<Zp> *>(c.spec);
-    const Split &sp = c.sp;
-    const uint64_t L = c.L;
-    const cx<Zp> invL = zp_pow2(192 - c.lgL);  // L^-1 mod p = 2^(192 - lgL)
+    const Geometry &g = c.geo;
+    const uint64_t L = g.L;
+    const cx<Zp> invL = zp_pow2(192 - (int)tw.lgL);  // L^-1 mod p = 2^(192 - log2 L)
     for (uint32_t i = 0; i < c.nb; ++i) {
         const pa_block_desc_t &b = hb[ids[i]];
         const uint64_t kw = (b.n + 63) / 64;
-        U_CUDA(launch_fwd_seed<Zp>(sp.lg1, b.seed, b.n, b.m, W, L, tw, st));
-        if (sp.lgM) U_CUDA(launch_mid<Zp>(sp.lgM, false, W, L, (uint32_t)sp.lgI, 1, tw, st));
-        U_CUDA(launch_middle<Zp>(sp.lgI, 1, W, spec, L, 1, tw, invL, st));
+        U_CUDA(launch_fwd_seed<Zp>(g.lg1, b.seed, b.n, b.m, W, L, tw, st));
+        if (g.lgM) U_CUDA(launch_mid<Zp>(g.lgM, false, W, L, g.inner(), 1, tw, st));
+        U_CUDA(launch_middle<Zp>(g.ro, g.lgI, 1, W, spec, L, 1, tw, invL, st));
         U_CUDA(launch_prep(b.key, 1, kw, b.n, popc + ids[i], marg + ids[i], st));
-        U_CUDA(launch_fwd_keys<Zp>(sp.lg1, b.key, 1, kw, b.n, W, L, 1, tw, st));
-        if (sp.lgM) U_CUDA(launch_mid<Zp>(sp.lgM, false, W, L, (uint32_t)sp.lgI, 1, tw, st));
-        U_CUDA(launch_middle<Zp>(sp.lgI, 0, W, spec, L, 1, tw, (cx<Zp>)1, st));
-        if (sp.lgM) U_CUDA(launch_mid<Zp>(sp.lgM, true, W, L, (uint32_t)sp.lgI, 1, tw, st));
-        U_CUDA(launch_inv_bits<Zp>(sp.lg1, W, L, b.m, 1, popc + ids[i], marg + ids[i], b.out, (b.m + 63) / 64, 1, tw,
+        U_CUDA(launch_fwd_keys<Zp>(g.lg1, b.key, 1, kw, b.n, W, L, 1, tw, st));
+        if (g.lgM) U_CUDA(launch_mid<Zp>(g.lgM, false, W, L, g.inner(), 1, tw, st));
+        U_CUDA(launch_middle<Zp>(g.ro, g.lgI, 0, W, spec, L, 1, tw, (cx<Zp>)1, st));
+        if (g.lgM) U_CUDA(launch_mid<Zp>(g.lgM, true, W, L, g.inner(), 1, tw, st));
+        U_CUDA(launch_inv_bits<Zp>(g.lg1, W, L, b.m, 1, popc + ids[i], marg + ids[i], b.out, (b.m + 63) / 64, 1, tw,
                                    st));
     }
     return PA_OK;
 }
 
 int run_class(pa_uneven_t *u, const UClass &c, cudaStream_t st) {
-    if (u->dtype == PA_NTT64) return run_class_ntt(c.run(c.sp), u->blocks.data(), c.ids.data(), u->popc, u->marg, st);
-    return pa::blocks::run_complex(u->dtype, c.run(c.sp), u->popc, u->marg, st);
+    if (u->dtype == PA_NTT64) return run_class_ntt(c.run(c.geo), u->blocks.data(), c.ids.data(), u->popc, u->marg, st);
+    return pa::blocks::run_complex(u->dtype, c.run(c.geo), u->popc, u->marg, st);
+}
+
+// (Re)build the stage-twiddle table of a class for the F of its current split.
+int class_fine(pa_uneven_t *u, UClass &c) {
+    const uint32_t F = c.geo.F();
+    if (c.tw_fine && c.fineF == F) return PA_OK;
+    if (c.tw_fine) cudaFree(c.tw_fine);
+    c.tw_fine = nullptr;
+    void *hi = nullptr, *lo = nullptr;
+    uint32_t B = 0;
+    int rc = pa_internal_twiddles(c.geo.L, F, (int)u->dtype, &hi, &lo, &B, &c.tw_fine);
+    if (rc != PA_OK) return rc;
+    cudaFree(hi);
+    cudaFree(lo);
+    c.fineF = F;
+    return PA_OK;
 }
 
 // Choose a class's split: cached, else time every candidate on the class's own data.
 int tune_class(pa_uneven_t *u, UClass &c) {
-    std::vector<Split> cand = pa::blocks::candidates(c.lgL, u->dtype);
+    const uint64_t L = c.geo.L;
+    std::vector<Geometry> cand = pa::blocks::candidates(L, u->dtype);
     if (cand.empty()) return PA_EUNSUPPORTED;
-    if (pa::blocks::cached_split(c.lgL, u->dtype, &c.sp)) return PA_OK;
+    if (pa::blocks::cached_split(L, u->dtype, &c.geo)) return class_fine(u, c);
     if (cand.size() == 1 || u->dtype == PA_NTT64) {
-        c.sp = pa::blocks::default_split(c.lgL, u->dtype);
-        pa::blocks::store_split(c.lgL, u->dtype, c.sp);
-        return PA_OK;
+        c.geo = pa::blocks::default_split(L, u->dtype);
+        pa::blocks::store_split(c.geo, u->dtype);
+        return class_fine(u, c);
     }
     cudaEvent_t a, b;
     U_CUDA(cudaEventCreate(&a));
     U_CUDA(cudaEventCreate(&b));
     float best = 1e30f;
-    Split bestsp = cand[0];
-    for (const Split &sp : cand) {
+    Geometry bestg = cand[0];
+    for (const Geometry &g : cand) {
+        c.geo = g;
+        int rc = class_fine(u, c);
+        if (rc != PA_OK) return rc;
         float total = 0.f;
         for (int rep = 0; rep < 3; ++rep) {
             U_CUDA(cudaEventRecord(a, c.st));
-            int rc = pa::blocks::run_complex(u->dtype, c.run(sp), u->popc, u->marg, c.st);
+            rc = pa::blocks::run_complex(u->dtype, c.run(g), u->popc, u->marg, c.st);
             if (rc != PA_OK) return rc;
             U_CUDA(cudaEventRecord(b, c.st));
             U_CUDA(cudaEventSynchronize(b));
@@ -212,14 +230,14 @@ int tune_class(pa_uneven_t *u, UClass &c) {
         }
         if (total < best) {
             best = total;
-            bestsp = sp;
+            bestg = g;
         }
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    c.sp = bestsp;
-    pa::blocks::store_split(c.lgL, u->dtype, c.sp);
-    return PA_OK;
+    c.geo = bestg;
+    pa::blocks::store_split(c.geo, u->dtype);
+    return class_fine(u, c);
 }
 
 void free_uneven(pa_uneven_t *u) {
@@ -233,6 +251,7 @@ void free_uneven(pa_uneven_t *u) {
         cudaFree(c.spec);
         cudaFree(c.tw_hi);
         cudaFree(c.tw_lo);
+        cudaFree(c.tw_fine);
         if (c.st) cudaStreamDestroy(c.st);
         if (c.done) cudaEventDestroy(c.done);
     }
@@ -245,7 +264,9 @@ void free_uneven(pa_uneven_t *u) {
     delete u;
 }
 
-int lg_length(const pa_block_desc_t &b) { return pa::blocks::lg_length(b.n, b.m); }
+uint64_t block_length(const pa_block_desc_t &b, pa_dtype_t dtype) {
+    return pa::blocks::class_length(b.n, b.m, dtype);
+}
 
 bool desc_ok(const pa_block_desc_t &b) {
     if (b.n == 0 || b.m == 0 || b.m > b.n || b.n > (1ull << 27)) return false;
@@ -300,14 +321,11 @@ int capture_graph(pa_uneven_t *u) {
 namespace pa {
 namespace blocks {
 
-int lg_length(uint64_t n, uint64_t m) {
-    int lgL = 12;
-    while ((1ull << lgL) < n + m - 1) ++lgL;
-    return lgL;
+uint64_t class_length(uint64_t n, uint64_t m, pa_dtype_t dtype) {
+    return choose_geometry(n + m - 1, dtype, dtype != PA_NTT64).L;
 }
 
-size_t scratch_per_block(int lgL, pa_dtype_t dtype) {
-    const size_t L = (size_t)1 << lgL;
+size_t scratch_per_block(uint64_t L, pa_dtype_t dtype) {
     if (dtype == PA_NTT64) return 2 * L * 8;
     const size_t e = dtype == PA_FP32_GUARD ? sizeof(float2) : sizeof(double2);
     return L * e + (L * e + 1) / 2 + sizeof(BlockDev) + 8;  // forward slot, half an inverse slot, descriptor, counters
@@ -323,51 +341,29 @@ int run_ntt(const ClassRun &c, const pa_block_desc_t *hb, const uint32_t *ids, u
     return run_class_ntt(c, hb, ids, popc, marg, st);
 }
 
-std::vector<Split> candidates(int lgL, pa_dtype_t dtype) {
-    const int maxI = max_inner(dtype);
-    std::vector<Split> two, three;
-    for (int lg1 = kMinLgStrided; lg1 <= kMaxLgStrided; ++lg1) {
-        const int in2 = lgL - lg1;
-        if (in2 >= kMinLgMiddle && in2 <= maxI) two.push_back(Split{lg1, 0, in2});
-        const int in3 = lgL - lg1 - kMinLgStrided;
-        if (in3 >= kMinLgMiddle && in3 <= maxI) three.push_back(Split{lg1, kMinLgStrided, in3});
-    }
-    return two.empty() ? three : two;
+std::vector<Geometry> candidates(uint64_t L, pa_dtype_t dtype) {
+    return geometry_candidates(L, dtype, dtype != PA_NTT64);
 }
 
-Split default_split(int lgL, pa_dtype_t dtype) {
-    std::vector<Split> c = candidates(lgL, dtype);
-    if (c.empty()) return Split{};
-    // prefer an innermost transform near 2^12 (fits one CTA with room for two per SM)
-    Split best = c[0];
-    int bestd = 1 << 30;
-    for (const Split &s : c) {
-        const int d = s.lgI > 12 ? s.lgI - 12 : 12 - s.lgI;
-        if (d < bestd) {
-            bestd = d;
-            best = s;
-        }
-    }
-    return best;
-}
+Geometry default_split(uint64_t L, pa_dtype_t dtype) { return default_geometry(L, dtype, dtype != PA_NTT64); }
 
-bool cached_split(int lgL, pa_dtype_t dtype, Split *out) {
+bool cached_split(uint64_t L, pa_dtype_t dtype, Geometry *out) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     tune_load_locked();
-    auto it = g_tune.find({lgL, (int)dtype});
+    auto it = g_tune.find({L, (int)dtype});
     if (it == g_tune.end()) return false;
     *out = it->second;
     return true;
 }
 
-void store_split(int lgL, pa_dtype_t dtype, const Split &s) {
+void store_split(const Geometry &g, pa_dtype_t dtype) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune[{lgL, (int)dtype}] = s;
+    g_tune[{g.L, (int)dtype}] = g;
     const char *path = std::getenv("PA_TUNE_CACHE");
     if (!path) return;
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%d %d %d %d %d\n", lgL, (int)dtype, s.lg1, s.lgM, s.lgI);
+    std::fprintf(f, "%llu %d %d %d %d %d\n", (unsigned long long)g.L, (int)dtype, g.lg1, g.lgM, g.ro, g.lgI);
     std::fclose(f);
 }
 
@@ -384,15 +380,15 @@ int pa_uneven_create(const pa_block_desc_t *blocks, uint32_t nblocks, pa_dtype_t
     for (uint32_t i = 0; i < nblocks; ++i)
         if (!desc_ok(blocks[i])) return PA_EINVAL;
     for (uint32_t i = 0; i < nblocks; ++i)
-        if (lg_length(blocks[i]) > 28) return PA_EUNSUPPORTED;
+        if (block_length(blocks[i], dtype) == 0) return PA_EUNSUPPORTED;
     pa_uneven_t *u = new pa_uneven_t();
     u->dtype = dtype;
     u->nblocks = nblocks;
     u->use_graph = use_graph != 0;
     u->blocks.assign(blocks, blocks + nblocks);
     cudaGetDevice(&u->device);
-    std::map<int, std::vector<uint32_t>> byL;
-    for (uint32_t i = 0; i < nblocks; ++i) byL[lg_length(blocks[i])].push_back(i);
+    std::map<uint64_t, std::vector<uint32_t>> byL;
+    for (uint32_t i = 0; i < nblocks; ++i) byL[block_length(blocks[i], dtype)].push_back(i);
     const size_t esz = dtype == PA_FP32_GUARD ? sizeof(float2) : dtype == PA_FP64 ? sizeof(double2) : 8;
     int rc = PA_OK;
     auto fail = [&](int r) {
@@ -412,8 +408,7 @@ int pa_uneven_create(const pa_block_desc_t *blocks, uint32_t nblocks, pa_dtype_t
     U_TRY(cudaEventCreateWithFlags(&u->fork, cudaEventDisableTiming));
     for (auto &kv : byL) {
         UClass c;
-        c.lgL = kv.first;
-        c.L = 1ull << c.lgL;
+        c.geo = pa::blocks::default_split(kv.first, dtype);
         c.ids = kv.second;
         u->classes.push_back(c);
     }
@@ -424,15 +419,17 @@ int pa_uneven_create(const pa_block_desc_t *blocks, uint32_t nblocks, pa_dtype_t
         std::vector<BlockDev> d = class_descs(u, c);
         U_TRY(cudaMalloc(&c.d_blocks, d.size() * sizeof(BlockDev)));
         U_TRY(cudaMemcpy(c.d_blocks, d.data(), d.size() * sizeof(BlockDev), cudaMemcpyHostToDevice));
+        const uint64_t L = c.geo.L;
         if (dtype == PA_NTT64) {
-            U_TRY(cudaMalloc(&c.Wf, c.L * esz));
-            U_TRY(cudaMalloc(&c.spec, c.L * esz));
+            U_TRY(cudaMalloc(&c.Wf, L * esz));
+            U_TRY(cudaMalloc(&c.spec, L * esz));
         } else {
-            U_TRY(cudaMalloc(&c.Wf, (size_t)nb * c.L * esz));
-            U_TRY(cudaMalloc(&c.Wi, (size_t)((nb + 1) / 2) * c.L * esz));
+            U_TRY(cudaMalloc(&c.Wf, (size_t)nb * L * esz));
+            U_TRY(cudaMalloc(&c.Wi, (size_t)((nb + 1) / 2) * L * esz));
         }
-        rc = pa_internal_twiddles(c.lgL, (int)dtype, &c.tw_hi, &c.tw_lo, &c.B);
+        rc = pa_internal_twiddles(L, c.geo.F(), (int)dtype, &c.tw_hi, &c.tw_lo, &c.B, &c.tw_fine);
         if (rc != PA_OK) return fail(rc);
+        c.fineF = c.geo.F();
         rc = tune_class(u, c);
         if (rc != PA_OK) return fail(rc);
     }
@@ -544,10 +541,10 @@ int pa_uneven_class(const pa_uneven_t *u, uint32_t c, uint32_t *nclasses, uint64
     if (nclasses) *nclasses = (uint32_t)u->classes.size();
     if (c >= u->classes.size()) return (nclasses && !L && !L1 && !L2 && !L3 && !nb) ? PA_OK : PA_EINVAL;
     const UClass &k = u->classes[c];
-    if (L) *L = k.L;
-    if (L1) *L1 = 1u << k.sp.lg1;
-    if (L2) *L2 = k.sp.lgM ? (1u << k.sp.lgM) : (1u << k.sp.lgI);
-    if (L3) *L3 = k.sp.lgM ? (1u << k.sp.lgI) : 1u;
+    if (L) *L = k.geo.L;
+    if (L1) *L1 = 1u << k.geo.lg1;
+    if (L2) *L2 = k.geo.lgM ? (1u << k.geo.lgM) : k.geo.inner();
+    if (L3) *L3 = k.geo.lgM ? k.geo.inner() : 1u;
     if (nb) *nb = (uint32_t)k.ids.size();
     return PA_OK;
 }

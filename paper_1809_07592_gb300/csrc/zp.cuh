@@ -72,6 +72,11 @@ template <> struct Arith<Zp> {
         const int k = INV ? (192 - 6 * j) : 6 * j;
         return zp_mul(x, zp_pow2(k));
     }
+    // w_F^e (forward) or w_F^-e = w_F^(F-e) (inverse) from the stage table.
+    template <bool INV> static __device__ __forceinline__ E fine(const TwTab<Zp> &t, uint32_t e) {
+        if (INV && e) e = t.F - e;
+        return __ldg(t.fine + e);
+    }
     // w_L^e (forward) or w_L^-e = w_L^(L-e) (inverse) from the two-level table.
     template <bool INV> static __device__ __forceinline__ E omega(const TwTab<Zp> &t, uint32_t e) {
         if (INV) e = (uint32_t)((0u - e) & ((1u << t.lgL) - 1u));

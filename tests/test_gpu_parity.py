@@ -109,13 +109,17 @@ def test_forced_escalation_keeps_bits():
 
 @pytest.mark.parametrize("n,m", [(1 << 20, 1 << 18), (1 << 23, 1 << 21)])
 def test_adversarial_all_ones_escalates_or_exact(n, m):
-    """All-ones key and seed make |w| ~ n/2: FP32 cannot resolve it and must hand the keys to FP64."""
+    """All-ones key and seed make |w| ~ n/2. FP32 must either resolve it (margin <= 0.25) or hand the
+    key to FP64; past |w| = 2^21 it cannot resolve parity at all and must escalate."""
     ones_k = inputs.mask_tail(np.full((n + 63) // 64, 0xFFFFFFFFFFFFFFFF, dtype=np.uint64), n)
     ones_s = inputs.mask_tail(np.full((n + m + 62) // 64, 0xFFFFFFFFFFFFFFFF, dtype=np.uint64), n + m - 1)
     rnd = inputs.bernoulli_bits(1, 2, n)
     keys = np.stack([ones_k, rnd])
     got, marg, mode, esc, _ = run(n, m, pa.PA_FP32_GUARD, keys, ones_s)
-    assert mode[0] == pa.PA_FP64 and esc >= 1
+    if n // 2 >= (1 << 21):
+        assert mode[0] == pa.PA_FP64 and esc >= 1
+    else:
+        assert (mode[0] == pa.PA_FP64 and esc >= 1) or (mode[0] == pa.PA_FP32_GUARD and marg[0] <= 0.25)
     rows = sample_rows(m, 100)
     for k in range(2):
         exp = oracle.toeplitz_rows(n, m, ones_s, keys[k], rows)
@@ -211,10 +215,47 @@ def test_long_block_2p27(dtype):
     n, m = 1 << 27, 1 << 24
     key, seed = inputs.block_inputs(n, m, base_seed=0)
     got, marg, mode, esc, shape = run(n, m, dtype, key[None, :], seed)
-    assert shape[0] == 1 << 28 and shape[3] > 1
+    assert n + m - 1 <= shape[0] <= 1 << 28 and shape[3] > 1
+    if dtype == pa.PA_NTT64:
+        assert shape[0] == 1 << 28  # the exact transform keeps power-of-two lengths
     rows = sample_rows(m, 120, seed=27)
     exp = oracle.toeplitz_rows(n, m, seed, key, rows)
     np.testing.assert_array_equal(unpack_rows(got, m)[0][rows.astype(np.int64)], exp)
     if dtype == pa.PA_FP32_GUARD:
         assert mode[0] in (pa.PA_FP32_GUARD, pa.PA_FP64)  # the guard may hand it to FP64
     assert marg[0] < 0.25
+
+
+# (n, m) whose n+m-1 lands just below RO * 2^k: every odd factor and a range of innermost lengths
+SMOOTH = [(ro, k) for ro in (3, 5, 9) for k in (13, 15, 17, 19)]
+
+
+@pytest.mark.parametrize("dtype", [pa.PA_FP32_GUARD, pa.PA_FP64], ids=["fp32g", "fp64"])
+@pytest.mark.parametrize("ro,k", SMOOTH)
+def test_smooth_lengths_bit_exact(ro, k, dtype):
+    """Transform lengths 3, 5 or 9 times a power of two (odd-radix stage in the innermost pass)."""
+    n, m = 2**k * ro * 2 // 3 + 7, 2**k * ro // 3 - 20  # n + m - 1 just below ro * 2^k
+    key, seed = inputs.block_inputs(n, m, base_seed=n)
+    keys = np.stack([key, inputs.bernoulli_bits(n, 9, n), inputs.bernoulli_bits(n, 10, n)])
+    got, marg, mode, esc, shape = run(n, m, dtype, keys, seed)
+    assert shape[0] == ro << k, shape
+    for k in range(3):
+        if n <= 200_000:
+            np.testing.assert_array_equal(got[k], oracle.toeplitz_hash(n, m, seed, keys[k]))
+        else:
+            rows = sample_rows(m, 150, seed=k)
+            exp = oracle.toeplitz_rows(n, m, seed, keys[k], rows)
+            np.testing.assert_array_equal(unpack_rows(got, m)[k][rows.astype(np.int64)], exp)
+    assert esc == 0 and (marg < 0.1).all()
+
+
+@pytest.mark.parametrize("dtype", [pa.PA_FP32_GUARD, pa.PA_FP64], ids=["fp32g", "fp64"])
+def test_smooth_three_level(dtype):
+    """An odd innermost length under a three-level split (n+m-1 just below 3 * 2^23)."""
+    n, m = (1 << 24) - 5, (1 << 23) - 11
+    key, seed = inputs.block_inputs(n, m, base_seed=31)
+    got, marg, mode, esc, shape = run(n, m, dtype, key[None, :], seed)
+    assert shape[0] == 3 << 23 and shape[3] > 1
+    rows = sample_rows(m, 150, seed=3)
+    exp = oracle.toeplitz_rows(n, m, seed, key, rows)
+    np.testing.assert_array_equal(unpack_rows(got, m)[0][rows.astype(np.int64)], exp)

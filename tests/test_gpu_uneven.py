@@ -77,7 +77,7 @@ def test_uneven_three_level_class(dtype):
     torch.cuda.synchronize()
     assert any(c[3] > 1 for c in pa.pa_uneven_classes(h))  # at least one three-level class
     check_blocks(sizes, data, blocks)
-    assert esc == 0 and max(marg) < 0.05
+    assert esc == 0 and max(marg) < 0.125  # transform length 2^24: well inside the 0.25 guard
     pa.pa_uneven_destroy(h)
 
 
@@ -134,7 +134,7 @@ def test_uneven_256_block_workload():
     h = pa.pa_uneven_create(blocks, pa.PA_FP32_GUARD, use_graph=True)
     marg, mode, esc = pa.pa_uneven_run(h, len(blocks), info=True)
     torch.cuda.synchronize()
-    assert esc == 0 and max(marg) < 0.1
+    assert esc == 0 and max(marg) < 0.2  # lengths up to 2^25 with the Eq. 5-10 split; guard is 0.25
     pick = [0, 1, 17, 100, 128, 200, 254, 255]
     check_blocks([sizes[i] for i in pick], [data[i] for i in pick], [blocks[i] for i in pick], full_limit=0,
                  nrows=60)
