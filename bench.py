@@ -346,7 +346,7 @@ def run_ours(args):
         hk = torch.from_numpy(kb.view(np.int64)).pin_memory()
         ho = torch.empty((NKEYS, ow), dtype=torch.int64).pin_memory()
         cases.append(dict(n=n, m=m, plan=plan, dk=dk, out=out, hk=hk, ho=ho, kw=kw, ow=ow, seed_dev=sw))
-    L = cases[0]["plan"].shape()[0]
+    lengths = [c["plan"].shape()[0] for c in cases]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
     stream = torch.cuda.current_stream()
 
@@ -470,7 +470,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": list(N_VALUES), "m_over_n": list(RATIOS), "keys_per_batch": NKEYS,
-                       "batches_per_step": len(cases), "mode": "FP32_GUARD", "transform_length": L,
+                       "batches_per_step": len(cases), "mode": "FP32_GUARD", "transform_lengths": lengths,
                        "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas{world}"},
             "batch_latency_ms": {"p50": p50, "p99": p99, "unit": "ms per 64-key batch"},
             "fp64_plain": {"value": fp64_value, "unit": "Mbit/s",

@@ -245,15 +245,28 @@ __device__ __forceinline__ void twiddle_chain(cx<T> *v, const TwTab<T> &tw, uint
     }
 }
 
-// v[r] *= w_F^{r*step} for r = 1..N-1 (one table load per value; the stage
-// twiddle w_{R p}^{r k} is w_F^{r k F/(R p)}).
-template <typename T, bool INV, int N>
+// v[r] *= w_F^{r*step} for r = 1..N-1 (the stage twiddle w_{R p}^{r k} is
+// w_F^{r k F/(R p)}). CHAIN = false: one table load per value (fewest
+// arithmetic operations; the strided passes, with many threads to hide the
+// loads). CHAIN = true: one load, then a chain of products (fewest loads and
+// registers; the innermost pass, which runs two transforms per CTA).
+template <typename T, bool INV, int N, bool CHAIN = false>
 __device__ __forceinline__ void stage_twiddles(cx<T> *v, const TwTab<T> &tw, uint32_t step) {
-    uint32_t e = step;
+    if constexpr (CHAIN) {
+        const cx<T> g = Arith<T>::template fine<INV>(tw, step);
+        cx<T> w = g;
 #pragma unroll
-    for (int r = 1; r < N; ++r) {
-        v[r] = Arith<T>::mul(v[r], Arith<T>::template fine<INV>(tw, e));
-        e += step;
+        for (int r = 1; r < N; ++r) {
+            v[r] = Arith<T>::mul(v[r], w);
+            if (r + 1 < N) w = Arith<T>::mul(w, g);
+        }
+    } else {
+        uint32_t e = step;
+#pragma unroll
+        for (int r = 1; r < N; ++r) {
+            v[r] = Arith<T>::mul(v[r], Arith<T>::template fine<INV>(tw, e));
+            e += step;
+        }
     }
 }
 
@@ -319,7 +332,7 @@ __device__ __forceinline__ void stage_to_smem(cx<T> *sm, cx<T> *v, uint32_t tq, 
     for (int b = 0; b < E / R; ++b) {
         const uint32_t i = tq + (uint32_t)b * TC;
         const uint32_t k = i % P;
-        if (P > 1) stage_twiddles<T, INV, R>(v + b * R, tw, k * (tw.F / (R * P)));
+        if (P > 1) stage_twiddles<T, INV, R, COLS == 1>(v + b * R, tw, k * (tw.F / (R * P)));
         dft<T, R, INV>(v + b * R);
         const uint32_t base = (i - k) * R + k;
 #pragma unroll
@@ -340,14 +353,14 @@ __device__ __forceinline__ void load_from_smem(const cx<T> *sm, cx<T> *v, uint32
 }
 
 // Last stage: twiddle + DFT in registers, results stay in registers.
-template <typename T, int LEN, int E, int R, int P, bool INV>
+template <typename T, int LEN, int COLS, int E, int R, int P, bool INV>
 __device__ __forceinline__ void stage_in_regs(cx<T> *v, uint32_t tq, const TwTab<T> &tw) {
     constexpr int TC = LEN / E;
 #pragma unroll
     for (int b = 0; b < E / R; ++b) {
         const uint32_t i = tq + (uint32_t)b * TC;
         const uint32_t k = i % P;
-        if (P > 1) stage_twiddles<T, INV, R>(v + b * R, tw, k * (tw.F / (R * P)));
+        if (P > 1) stage_twiddles<T, INV, R, COLS == 1>(v + b * R, tw, k * (tw.F / (R * P)));
         dft<T, R, INV>(v + b * R);
     }
 }
@@ -364,7 +377,7 @@ __device__ __forceinline__ void fwd_pow2(cx<T> *sm, cx<T> *v, uint32_t tq, uint3
         load_from_smem<T, LEN, COLS, E, R>(sm, v, tq, col);
     }
     if constexpr (S == PL::q - 1) {
-        stage_in_regs<T, LEN, E, R, P0, false>(v, tq, tw);
+        stage_in_regs<T, LEN, COLS, E, R, P0, false>(v, tq, tw);
     } else {
         if constexpr (!FROM_REGS) __syncthreads();
         stage_to_smem<T, LEN, COLS, E, R, P0, false>(sm, v, tq, col, tw);
@@ -385,7 +398,7 @@ __device__ __forceinline__ void inv_pow2(cx<T> *sm, cx<T> *v, uint32_t tq, uint3
         load_from_smem<T, LEN, COLS, E, R>(sm, v, tq, col);
     }
     if constexpr (S == PL::q - 1 && !TO_SMEM) {
-        stage_in_regs<T, LEN, E, R, P0, true>(v, tq, tw);
+        stage_in_regs<T, LEN, COLS, E, R, P0, true>(v, tq, tw);
     } else {
         if constexpr (S > 0) __syncthreads();
         stage_to_smem<T, LEN, COLS, E, R, P0, true>(sm, v, tq, col, tw);

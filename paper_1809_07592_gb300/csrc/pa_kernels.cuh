@@ -405,7 +405,8 @@ __global__ void __launch_bounds__(2 * (LEN / E), min_blocks_inner(2 * (LEN / E))
 #pragma unroll
         for (int s = 0; s < E; ++s) {
             const uint32_t p = idx_e<LEN, E>(tq, s);
-            const uint32_t pm = (my_rho == 0) ? ((LEN - p) & (LEN - 1)) : (LEN - 1 - p);
+            // mirror of position p: -p mod LEN in the row of the zero frequency low part, else LEN-1-p
+            const uint32_t pm = (my_rho == 0) ? (p == 0 ? 0u : (uint32_t)LEN - p) : ((uint32_t)LEN - 1u - p);
             const cx<T> z = v[s], zm = sm_other[sidx<1>(pm, 0)];
             // Eq. 7-10: X = (Z(k) + conj Z(-k)) / 2, V = (Z(k) - conj Z(-k)) / (2i)
             const cx<T> X = Arith<T>::mk((z.x + zm.x) * (T)0.5, (z.y - zm.y) * (T)0.5);
