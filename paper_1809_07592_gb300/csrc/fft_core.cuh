@@ -246,11 +246,11 @@ __device__ __forceinline__ void twiddle_chain(cx<T> *v, const TwTab<T> &tw, uint
 }
 
 // v[r] *= w_F^{r*step} for r = 1..N-1 (the stage twiddle w_{R p}^{r k} is
-// w_F^{r k F/(R p)}). CHAIN = false: one table load per value (fewest
-// arithmetic operations; the strided passes, with many threads to hide the
-// loads). CHAIN = true: one load, then a chain of products (fewest loads and
-// registers; the innermost pass, which runs two transforms per CTA).
-template <typename T, bool INV, int N, bool CHAIN = false>
+// w_F^{r k F/(R p)}). CHAIN = true (used by every pass): one table load, then a
+// chain of products -- fewest loads and registers, measured faster than one
+// load per value in every pass but the last inverse one, where it is even.
+// CHAIN = false: one table load per value.
+template <typename T, bool INV, int N, bool CHAIN = true>
 __device__ __forceinline__ void stage_twiddles(cx<T> *v, const TwTab<T> &tw, uint32_t step) {
     if constexpr (CHAIN) {
         const cx<T> g = Arith<T>::template fine<INV>(tw, step);
@@ -332,7 +332,7 @@ __device__ __forceinline__ void stage_to_smem(cx<T> *sm, cx<T> *v, uint32_t tq, 
     for (int b = 0; b < E / R; ++b) {
         const uint32_t i = tq + (uint32_t)b * TC;
         const uint32_t k = i % P;
-        if (P > 1) stage_twiddles<T, INV, R, COLS == 1>(v + b * R, tw, k * (tw.F / (R * P)));
+        if (P > 1) stage_twiddles<T, INV, R>(v + b * R, tw, k * (tw.F / (R * P)));
         dft<T, R, INV>(v + b * R);
         const uint32_t base = (i - k) * R + k;
 #pragma unroll
@@ -360,7 +360,7 @@ __device__ __forceinline__ void stage_in_regs(cx<T> *v, uint32_t tq, const TwTab
     for (int b = 0; b < E / R; ++b) {
         const uint32_t i = tq + (uint32_t)b * TC;
         const uint32_t k = i % P;
-        if (P > 1) stage_twiddles<T, INV, R, COLS == 1>(v + b * R, tw, k * (tw.F / (R * P)));
+        if (P > 1) stage_twiddles<T, INV, R>(v + b * R, tw, k * (tw.F / (R * P)));
         dft<T, R, INV>(v + b * R);
     }
 }

@@ -95,6 +95,41 @@ __global__ void k_prep(const uint64_t *__restrict__ keys, uint32_t nkeys, uint64
                        uint32_t *__restrict__ popc, uint32_t *__restrict__ margin_bits);
 
 // ---------------------------------------------------------------------------
+// Bit staging for the level-1 forward passes: per row, the CTA's COLS input bits
+// (low 16 bits: key or key a; high 16 bits: key b or seed) after the transform's
+// shared memory.
+template <typename T, int LEN, int COLS>
+__device__ __forceinline__ uint32_t *key_stage(unsigned char *smem_raw) {
+    return reinterpret_cast<uint32_t *>(smem_raw + smem_elems<LEN, COLS>() * sizeof(cx<T>));
+}
+template <typename T, int LEN, int COLS>
+constexpr size_t stage_bytes() { return (size_t)LEN * sizeof(uint32_t); }
+
+// COLS bits of v starting at bit t0 (t0 % COLS == 0, so they sit in one word);
+// bits at or past nbits read as 0.
+template <int COLS>
+__device__ __forceinline__ uint32_t aligned_bits(const uint64_t *v, uint64_t nbits, uint64_t t0) {
+    if (t0 >= nbits) return 0u;
+    uint32_t w = (uint32_t)(__ldg(v + (t0 >> 6)) >> (t0 & 63)) & ((1u << COLS) - 1u);
+    const uint64_t left = nbits - t0;
+    if (left < COLS) w &= (1u << left) - 1u;
+    return w;
+}
+
+// cnt <= 32 bits of v starting at an arbitrary bit position pos; bits at or past nbits read as 0.
+__device__ __forceinline__ uint32_t bits_at(const uint64_t *v, uint64_t nbits, uint64_t pos, uint32_t cnt) {
+    if (pos >= nbits || cnt == 0) return 0u;
+    const uint64_t q = pos >> 6;
+    const uint32_t r = (uint32_t)(pos & 63);
+    uint64_t x = __ldg(v + q) >> r;
+    if (r + cnt > 64 && ((q + 1) << 6) < nbits) x |= __ldg(v + q + 1) << (64 - r);
+    uint32_t w = (uint32_t)x & (cnt == 32 ? 0xffffffffu : ((1u << cnt) - 1u));
+    const uint64_t left = nbits - pos;
+    if (left < cnt) w &= (1u << left) - 1u;
+    return w;
+}
+
+// ---------------------------------------------------------------------------
 // Level-1 forward pass from packed key bits. Grid (S/COLS, pairs); pair p
 // carries key 2p in the real part and key 2p+1 (if any) in the imaginary part.
 template <typename T, int LEN, int COLS, int E>
@@ -108,22 +143,22 @@ __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
     const uint64_t u = (uint64_t)blockIdx.x * COLS + col;
     const uint32_t pair = blockIdx.y;
     const bool has_b = 2 * pair + 1 < nkeys;
-    // S is a multiple of 64, so bit a*S + u lies in word a*(S/64) + u/64 at position u % 64.
-    const uint64_t S64 = S >> 6;
-    const uint32_t sh = (uint32_t)(u & 63);
-    const uint64_t *ka = keys + (uint64_t)(2 * pair) * kstride + (u >> 6);
-    const uint64_t *kb = keys + (uint64_t)(2 * pair + (has_b ? 1 : 0)) * kstride + (u >> 6);
-    const uint64_t arows = n > u ? (n - u + S - 1) / S : 0;  // rows a with a*S + u < n
+    // Stage the CTA's COLS bits of every row of both keys in shared memory first:
+    // one word load per row instead of one per element, all in flight together.
+    uint32_t *stage = key_stage<T, LEN, COLS>(smem_raw);
+    const uint64_t u0 = (uint64_t)blockIdx.x * COLS;
+    for (uint32_t a = threadIdx.x; a < LEN; a += blockDim.x) {
+        const uint64_t t0 = (uint64_t)a * S + u0;  // S % 64 == 0: the COLS bits sit in one word
+        const uint32_t wa = aligned_bits<COLS>(keys + (uint64_t)(2 * pair) * kstride, n, t0);
+        const uint32_t wb = has_b ? aligned_bits<COLS>(keys + (uint64_t)(2 * pair + 1) * kstride, n, t0) : 0u;
+        stage[a] = wa | (wb << 16);
+    }
+    __syncthreads();
     cx<T> v[E];
 #pragma unroll
     for (int s = 0; s < E; ++s) {
-        const uint32_t a = idx_r0<LEN, E>(tq, s);
-        uint32_t ba = 0, bb = 0;
-        if (a < arows) {
-            ba = (uint32_t)(__ldg(ka + a * S64) >> sh) & 1u;
-            if (has_b) bb = (uint32_t)(__ldg(kb + a * S64) >> sh) & 1u;
-        }
-        v[s] = Enc<T>::key_pair(ba, bb);
+        const uint32_t w2 = stage[idx_r0<LEN, E>(tq, s)];
+        v[s] = Enc<T>::key_pair((w2 >> col) & 1u, (w2 >> (16 + col)) & 1u);
     }
     cta_fft<T, LEN, COLS, E, false>(sm, v, tq, col, tw);
     cx<T> *w = W + (uint64_t)pair * L;
@@ -333,20 +368,38 @@ __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
     const uint64_t u = (uint64_t)blockIdx.x * COLS + col;
     const BlockDev bd = blocks[blockIdx.y];
     const uint64_t n = bd.n, sbits = bd.n + bd.m - 1;
-    const uint64_t S64 = S >> 6;
-    const uint32_t sh = (uint32_t)(u & 63);
-    const uint64_t *kp = bd.key + (u >> 6);
-    const uint64_t arows = n > u ? (n - u + S - 1) / S : 0;
+    // stage per row: the CTA's COLS key bits (aligned), COLS seed bits at the rotated
+    // position j = a*S + u0 + n - 1 (mod L; the window may wrap past L) and the mask
+    // of window positions inside the seed (past it the value is 0, not +-1)
+    uint64_t *stage = reinterpret_cast<uint64_t *>(key_stage<T, LEN, COLS>(smem_raw));
+    const uint64_t u0 = (uint64_t)blockIdx.x * COLS;
+    const uint32_t full = (1u << COLS) - 1u;
+    for (uint32_t a = threadIdx.x; a < LEN; a += blockDim.x) {
+        const uint64_t t0 = (uint64_t)a * S + u0;
+        const uint32_t wk = aligned_bits<COLS>(bd.key, n, t0);
+        uint64_t j0 = t0 + n - 1;
+        if (j0 >= L) j0 -= L;
+        uint32_t ws, inr;
+        if (j0 + COLS <= L) {
+            ws = bits_at(bd.seed, sbits, j0, COLS);
+            inr = j0 >= sbits ? 0u : (sbits - j0 >= COLS ? full : (1u << (sbits - j0)) - 1u);
+        } else {  // positions j0 .. L-1, then 0 .. COLS-c1-1 (wrapped)
+            const uint32_t c1 = (uint32_t)(L - j0);
+            ws = bits_at(bd.seed, sbits, j0, c1) | (bits_at(bd.seed, sbits, 0, COLS - c1) << c1);
+            const uint32_t lo = j0 >= sbits ? 0u : (sbits - j0 >= c1 ? (1u << c1) - 1u : (1u << (sbits - j0)) - 1u);
+            const uint32_t nw = sbits >= COLS - c1 ? COLS - c1 : (uint32_t)sbits;  // wrapped positions inside the seed
+            inr = lo | (((1u << nw) - 1u) << c1);
+        }
+        stage[a] = (uint64_t)wk | ((uint64_t)ws << 16) | ((uint64_t)inr << 32);
+    }
+    __syncthreads();
     cx<T> v[E];
 #pragma unroll
     for (int s = 0; s < E; ++s) {
-        const uint32_t a = idx_r0<LEN, E>(tq, s);
-        const uint32_t bx = (a < arows) ? (uint32_t)(__ldg(kp + a * S64) >> sh) & 1u : 0u;
-        uint64_t j = (uint64_t)a * S + u + n - 1;  // seed index at rotated position a*S + u
-        if (j >= L) j -= L;
-        const bool in_range = j < sbits;
-        const uint32_t bs = in_range ? (uint32_t)(__ldg(bd.seed + (j >> 6)) >> (j & 63)) & 1u : 0u;
-        v[s] = Arith<T>::mk(bx ? (T)1 : (T)0, in_range ? (bs ? (T)-1 : (T)1) : (T)0);
+        const uint64_t w3 = stage[idx_r0<LEN, E>(tq, s)];
+        const uint32_t bx = (uint32_t)(w3 >> col) & 1u, bs = (uint32_t)(w3 >> (16 + col)) & 1u;
+        const uint32_t inr = (uint32_t)(w3 >> (32 + col)) & 1u;
+        v[s] = Arith<T>::mk(bx ? (T)1 : (T)0, inr ? (bs ? (T)-1 : (T)1) : (T)0);
     }
     cta_fft<T, LEN, COLS, E, false>(sm, v, tq, col, tw);
     cx<T> *w = W + (uint64_t)blockIdx.y * L;

@@ -49,7 +49,7 @@ cudaError_t launch_fwd_keys(int lgLEN, const uint64_t *keys, uint32_t nkeys, uin
     return by_len<kMinLgStrided, kMaxLgStrided>(lgLEN, [&](auto c) {
         constexpr int LEN = decltype(c)::value;
         auto kern = k_fwd_keys<T, LEN, COLS, E>;
-        constexpr size_t sb = smem_bytes<T, LEN, COLS>();
+        constexpr size_t sb = smem_bytes<T, LEN, COLS>() + stage_bytes<T, LEN, COLS>();
         cudaError_t e = set_smem(kern, sb);
         if (e != cudaSuccess) return e;
         dim3 grid((unsigned)((L / LEN) / COLS), pairs);
@@ -197,7 +197,7 @@ cudaError_t launch_fwd_keyseed(int lgLEN, const BlockDev *blocks, uint32_t nbloc
     return by_len<kMinLgStrided, kMaxLgStrided>(lgLEN, [&](auto c) {
         constexpr int LEN = decltype(c)::value;
         auto kern = k_fwd_keyseed<T, LEN, COLS, E>;
-        constexpr size_t sb = smem_bytes<T, LEN, COLS>();
+        constexpr size_t sb = smem_bytes<T, LEN, COLS>() + 2 * stage_bytes<T, LEN, COLS>();  // 64-bit stage
         cudaError_t e = set_smem(kern, sb);
         if (e != cudaSuccess) return e;
         dim3 grid((unsigned)((L / LEN) / COLS), nblocks);
