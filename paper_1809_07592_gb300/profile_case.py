@@ -1,0 +1,48 @@
+"""One hash batch for profilers: ``python -m paper_1809_07592_gb300.profile_case``.
+
+Sets up one plan (seed spectrum computed) and hashes one batch of keys, so an
+external profiler run (``ncu -k regex:... -c N``) sees exactly one launch of each
+pass kernel after the seed transform. Inputs are the seeded synthetic keys of
+``inputs.py``; the CUDA path runs through the C ABI as in any other call.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+import numpy as np
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=1 << 20)
+    ap.add_argument("--m", type=int, default=1 << 18)
+    ap.add_argument("--keys", type=int, default=32)
+    ap.add_argument("--dtype", default="fp32_guard", choices=["fp32_guard", "fp64", "ntt64"])
+    a = ap.parse_args(argv)
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import torch
+
+    import paper_1809_07592_gb300 as pa
+    from paper_1809_07592_gb300 import inputs
+
+    torch.cuda.set_device(0)
+    seed = inputs.bernoulli_bits(0, inputs.STREAM_SEED, a.n + a.m - 1)
+    keys = inputs.batch_keys(a.n, a.keys, 0)
+    kw = keys.shape[1] + (keys.shape[1] & 1)
+    kb = np.zeros((a.keys, kw), np.uint64)
+    kb[:, : keys.shape[1]] = keys
+    sw = np.zeros(seed.size + (seed.size & 1), np.uint64)
+    sw[: seed.size] = seed
+    plan = pa.Plan(a.n, a.m, a.dtype)
+    plan.set_seed(torch.from_numpy(sw.view(np.int64)).cuda())
+    plan.hash(torch.from_numpy(kb.view(np.int64)).cuda())
+    torch.cuda.synchronize()
+    print("ok", plan.shape())
+    plan.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
