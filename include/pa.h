@@ -73,11 +73,16 @@ typedef struct {
 /*
  * pa_plan -- choose the transform for keys of n bits hashed to m bits.
  * Paper Section 2.2 (FFT length n+r-1 for the standard Toeplitz matrix) and
- * Algorithm 1 (a long FFT split into passes of short FFTs): the plan picks a
- * power-of-two complex length L >= n+m-1, factors it into two or three
- * passes, builds twiddle tables, and allocates the seed-spectrum slot (L
- * complex values) on the current CUDA device. Work buffers are allocated by the
- * first pa_hash_batch that needs them and kept until pa_plan_destroy.
+ * Algorithm 1 (a long FFT split into passes of short FFTs): the plan picks the
+ * smallest complex length L >= max(n+m-1, 4096) of the form ro * 2^k with ro in
+ * {1, 3, 5, 9} (ro = 1 only for PA_NTT64), factors it into two or three passes,
+ * builds twiddle tables, and allocates the seed-spectrum slot (L complex values)
+ * on the current CUDA device. Where L has several valid pass splits, the first
+ * plan of each (L, dtype) in a process times every split on a batch of zero keys
+ * (stream-ordered on a private stream, up to 32 key pairs; set the environment
+ * variable PA_PLAN_TUNE=0 to skip this and take the default split) and later
+ * plans reuse the winner. Work buffers are allocated by the first pa_hash_batch
+ * that needs them and kept until pa_plan_destroy.
  *   n      key length in bits, 1 <= n <= 2^27
  *   m      final-key length in bits, 1 <= m <= n
  *   dtype  arithmetic of the transform (see pa_dtype_t)
@@ -85,6 +90,21 @@ typedef struct {
  * Returns PA_EINVAL for bad sizes, PA_ENOMEM, PA_EUNSUPPORTED, PA_ECUDA.
  */
 int pa_plan(uint64_t n, uint64_t m, pa_dtype_t dtype, pa_plan_t **out);
+
+/*
+ * pa_plan_splits -- the pass splits pa_plan chooses among for (n, m, dtype) (no GPU work).
+ * Writes up to `cap` entries (L1[i], L2[i], L3[i]) in the convention of pa_plan_shape and
+ * the total number of splits to *count. Every split computes the same bits.
+ * Returns PA_EINVAL for bad arguments, PA_EUNSUPPORTED if no length is supported.
+ */
+int pa_plan_splits(uint64_t n, uint64_t m, pa_dtype_t dtype, uint32_t *L1, uint32_t *L2, uint32_t *L3, int cap,
+                   int *count);
+
+/*
+ * pa_plan_split -- pa_plan with the pass split fixed to (L1, L2, L3), one of the splits
+ * pa_plan_splits lists (PA_EINVAL otherwise). No timing is done.
+ */
+int pa_plan_split(uint64_t n, uint64_t m, pa_dtype_t dtype, uint32_t L1, uint32_t L2, uint32_t L3, pa_plan_t **out);
 
 /* Release a plan and all device memory it owns. NULL is accepted. Synchronizes the device. */
 int pa_plan_destroy(pa_plan_t *plan);
@@ -114,9 +134,32 @@ int pa_set_seed(pa_plan_t *plan, const uint64_t *seed_dev, uint64_t seed_bits, p
  * call waits for the stream to read the rounding margins back (the guard of
  * Section 5's precision question needs them on the host); otherwise it returns
  * after issuing the kernels. Returns PA_ENOSEED if no seed was set.
+ * Device waits are bounded: the fused convolution kernel waits on its own
+ * asynchronous copies for at most 1 s. If a wait runs out, the plan's device
+ * error word is set and the next call that synchronizes (this one in
+ * PA_FP32_GUARD mode or with info) returns PA_ETIMEOUT, clears the word, and the
+ * outputs of the batches since the last synchronizing call are not valid.
  */
 int pa_hash_batch(pa_plan_t *plan, const uint64_t *keys_dev, uint32_t nkeys, uint64_t key_stride_words,
                   uint64_t *out_dev, uint64_t out_stride_words, pa_stream_t stream, pa_batch_info_t *info);
+
+/*
+ * pa_hash_batch_async / pa_batch_finish -- pa_hash_batch in two halves, so that a
+ * host thread can issue batches of several plans back to back and run the
+ * guard of each afterwards (no idle GPU between batches).
+ * pa_hash_batch_async checks the arguments as pa_hash_batch does, issues the
+ * kernels and the read-back of the rounding margins on the stream, and returns.
+ * pa_batch_finish waits for that read-back, recomputes every key whose margin
+ * fails the guard one mode wider (as pa_hash_batch does) and fills info (may be
+ * NULL). The outputs are final once pa_batch_finish has returned PA_OK. Between
+ * the two calls the plan accepts no other hash call (PA_EAGAIN); pa_batch_finish
+ * without an issued batch returns PA_EINVAL. pa_hash_batch is
+ * pa_hash_batch_async followed by pa_batch_finish (the latter skipped in
+ * PA_FP64 / PA_NTT64 mode without info).
+ */
+int pa_hash_batch_async(pa_plan_t *plan, const uint64_t *keys_dev, uint32_t nkeys, uint64_t key_stride_words,
+                        uint64_t *out_dev, uint64_t out_stride_words, pa_stream_t stream);
+int pa_batch_finish(pa_plan_t *plan, pa_batch_info_t *info);
 
 /*
  * pa_plan_set_guard -- rounding-margin threshold of the FP32 guard (default 0.25,

@@ -97,8 +97,13 @@ def lib():
     L.pa_set_seed.argtypes = [vp, vp, u64, vp]
     L.pa_hash_batch.argtypes = [vp, vp, u32, u64, vp, u64, vp, ctypes.POINTER(BatchInfo)]
     L.pa_plan_set_guard.argtypes = [vp, ctypes.c_float]
+    L.pa_hash_batch_async.argtypes = [vp, vp, u32, u64, vp, u64, vp]
+    L.pa_batch_finish.argtypes = [vp, ctypes.POINTER(BatchInfo)]
     L.pa_plan_shape.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u32), ctypes.POINTER(u32),
                                 ctypes.POINTER(u32)]
+    L.pa_plan_splits.argtypes = [u64, u64, ctypes.c_int, ctypes.POINTER(u32), ctypes.POINTER(u32),
+                                 ctypes.POINTER(u32), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    L.pa_plan_split.argtypes = [u64, u64, ctypes.c_int, u32, u32, u32, ctypes.POINTER(vp)]
     L.pa_profile_enable.argtypes = [vp, ctypes.c_int]
     L.pa_profile_read.argtypes = [vp, ctypes.POINTER(KernelStat), ctypes.POINTER(ctypes.c_int), ctypes.c_int]
     bdp = ctypes.POINTER(BlockDesc)
@@ -120,8 +125,9 @@ def lib():
     L.pa_strerror.restype = ctypes.c_char_p
     L.pa_last_cuda_error.argtypes = []
     L.pa_last_cuda_error.restype = ctypes.c_char_p
-    for name in ("pa_plan", "pa_plan_destroy", "pa_set_seed", "pa_hash_batch", "pa_plan_set_guard",
-                 "pa_plan_shape", "pa_profile_enable", "pa_profile_read", "pa_uneven_create", "pa_uneven_update",
+    for name in ("pa_plan", "pa_plan_destroy", "pa_set_seed", "pa_hash_batch", "pa_hash_batch_async",
+                 "pa_batch_finish", "pa_plan_set_guard",
+                 "pa_plan_shape", "pa_plan_splits", "pa_plan_split", "pa_profile_enable", "pa_profile_read", "pa_uneven_create", "pa_uneven_update",
                  "pa_uneven_run", "pa_uneven_set_guard", "pa_uneven_destroy", "pa_uneven_class", "pa_hash_uneven",
                  "pa_server_create", "pa_submit", "pa_poll", "pa_wait", "pa_server_stats", "pa_server_destroy"):
         getattr(L, name).restype = ctypes.c_int
@@ -161,6 +167,27 @@ def pa_plan(n: int, m: int, dtype=PA_FP32_GUARD) -> int:
     return h.value
 
 
+def pa_plan_splits(n: int, m: int, dtype=PA_FP32_GUARD):
+    """The pass splits (L1, L2, L3) a plan of (n, m, dtype) chooses among."""
+    if isinstance(dtype, str):
+        dtype = DTYPES[dtype]
+    cnt = ctypes.c_int()
+    _check(lib().pa_plan_splits(n, m, dtype, None, None, None, 0, ctypes.byref(cnt)), "pa_plan_splits")
+    k = cnt.value
+    a, b, c = (ctypes.c_uint32 * max(k, 1))(), (ctypes.c_uint32 * max(k, 1))(), (ctypes.c_uint32 * max(k, 1))()
+    _check(lib().pa_plan_splits(n, m, dtype, a, b, c, k, ctypes.byref(cnt)), "pa_plan_splits")
+    return [(a[i], b[i], c[i]) for i in range(k)]
+
+
+def pa_plan_split(n: int, m: int, dtype, split) -> int:
+    """pa_plan with the pass split fixed to one of pa_plan_splits' entries."""
+    if isinstance(dtype, str):
+        dtype = DTYPES[dtype]
+    h = ctypes.c_void_p()
+    _check(lib().pa_plan_split(n, m, dtype, split[0], split[1], split[2], ctypes.byref(h)), "pa_plan_split")
+    return h.value
+
+
 def pa_plan_destroy(plan: int) -> None:
     _check(lib().pa_plan_destroy(plan), "pa_plan_destroy")
 
@@ -194,6 +221,26 @@ def pa_hash_batch(plan: int, keys, nkeys: int, key_stride_words: int, out, out_s
         return list(marg), list(mode), bi.escalated
     _check(lib().pa_hash_batch(plan, _ptr(keys), nkeys, key_stride_words, _ptr(out), out_stride_words,
                                _stream_handle(stream), None), "pa_hash_batch")
+    return None
+
+
+def pa_hash_batch_async(plan: int, keys, nkeys: int, key_stride_words: int, out, out_stride_words: int,
+                        stream=None) -> None:
+    """Issue a batch (kernels + margin read-back) without waiting; finish it with pa_batch_finish."""
+    _check(lib().pa_hash_batch_async(plan, _ptr(keys), nkeys, key_stride_words, _ptr(out), out_stride_words,
+                                     _stream_handle(stream)), "pa_hash_batch_async")
+
+
+def pa_batch_finish(plan: int, nkeys: int = 0, info: bool = False):
+    """Guard step of an issued batch; (margins, modes, escalated) when ``info`` is set (nkeys needed)."""
+    if info:
+        marg = (ctypes.c_float * nkeys)()
+        mode = (ctypes.c_int32 * nkeys)()
+        bi = BatchInfo(ctypes.cast(marg, ctypes.POINTER(ctypes.c_float)),
+                       ctypes.cast(mode, ctypes.POINTER(ctypes.c_int32)), 0, 0)
+        _check(lib().pa_batch_finish(plan, ctypes.byref(bi)), "pa_batch_finish")
+        return list(marg), list(mode), bi.escalated
+    _check(lib().pa_batch_finish(plan, None), "pa_batch_finish")
     return None
 
 
@@ -330,9 +377,9 @@ def pa_server_destroy(server: int) -> None:
 class Plan:
     """Owns one pa_plan handle; a convenience wrapper over the functions above."""
 
-    def __init__(self, n: int, m: int, dtype=PA_FP32_GUARD):
+    def __init__(self, n: int, m: int, dtype=PA_FP32_GUARD, split=None):
         self.n, self.m = n, m
-        self.handle = pa_plan(n, m, dtype)
+        self.handle = pa_plan(n, m, dtype) if split is None else pa_plan_split(n, m, dtype, split)
 
     def words_in(self) -> int:
         return (self.n + 63) // 64

@@ -121,6 +121,113 @@ __device__ __forceinline__ void dft_odd(cx<T> *x) {
     }
 }
 
+// cos and sin of 2 pi a / b in double precision at compile time: the angle is
+// reduced to [0, pi/4] by the symmetries of the circle, then summed as a Taylor
+// series (terms up to x^27 / 27!, below 1e-30 for |x| <= pi/4).
+__host__ __device__ constexpr double taylor_sin(double x) {
+    double term = x, sum = x;
+    for (int k = 1; k <= 13; ++k) {
+        term *= -x * x / ((2.0 * k) * (2.0 * k + 1.0));
+        sum += term;
+    }
+    return sum;
+}
+__host__ __device__ constexpr double taylor_cos(double x) {
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k <= 13; ++k) {
+        term *= -x * x / ((2.0 * k - 1.0) * (2.0 * k));
+        sum += term;
+    }
+    return sum;
+}
+constexpr double kPi = 3.14159265358979323846264338327950288;
+// cos (SIN = false) or sin (SIN = true) of 2 pi a / b for 0 <= a < b: with 4a = q b + r,
+// the angle is q pi/2 + psi, psi = (pi/2) r / b; psi above pi/4 is taken as
+// pi/2 - (pi/2)(b - r)/b so the series always runs on [0, pi/4].
+__host__ __device__ constexpr double trig_frac(int a, int b, bool want_sin) {
+    const int q = (4 * a) / b, r = (4 * a) % b;
+    const bool high = 2 * r > b;
+    const double psi = (kPi / 2.0) * (double)(high ? b - r : r) / (double)b;
+    const double c0 = high ? taylor_sin(psi) : taylor_cos(psi);
+    const double s0 = high ? taylor_cos(psi) : taylor_sin(psi);
+    // rotate (c0, s0) by q quarter turns
+    const double c = q == 0 ? c0 : q == 1 ? -s0 : q == 2 ? -c0 : s0;
+    const double sn = q == 0 ? s0 : q == 1 ? c0 : q == 2 ? -s0 : -c0;
+    return want_sin ? sn : c;
+}
+__host__ __device__ constexpr double cos_frac(int a, int b) { return trig_frac(a, b, false); }
+__host__ __device__ constexpr double sin_frac(int a, int b) { return trig_frac(a, b, true); }
+
+// x * w_N^J (forward root w_N = exp(-2 pi i / N); the inverse uses the conjugate),
+// with the half and quarter turns done exactly.
+template <typename T, int N, int J, bool INV>
+__device__ __forceinline__ cx<T> rot_const(cx<T> x) {
+    constexpr int j = J % N;
+    if constexpr (j == 0) {
+        return x;
+    } else if constexpr (2 * j == N) {
+        return Arith<T>::mk(-x.x, -x.y);
+    } else if constexpr (4 * j == N) {
+        return INV ? Arith<T>::mk(-x.y, x.x) : Arith<T>::mk(x.y, -x.x);
+    } else if constexpr (4 * j == 3 * N) {
+        return INV ? Arith<T>::mk(x.y, -x.x) : Arith<T>::mk(-x.y, x.x);
+    } else {
+        constexpr T c = (T)cos_frac(j, N);
+        constexpr T sn = (T)sin_frac(j, N);
+        constexpr T s = INV ? sn : -sn;
+        return Arith<T>::mk(x.x * c - x.y * s, x.x * s + x.y * c);
+    }
+}
+
+// a[n2 * RO + k1] *= w_{RO R0}^{n2 k1} for n2 >= N2, k1 >= K1 (compile-time indices).
+template <typename T, int RO, int R0, int N2, int K1, bool INV>
+__device__ __forceinline__ void comp_twiddle_row(cx<T> *a) {
+    if constexpr (K1 < RO) {
+        a[N2 * RO + K1] = rot_const<T, RO * R0, N2 * K1, INV>(a[N2 * RO + K1]);
+        comp_twiddle_row<T, RO, R0, N2, K1 + 1, INV>(a);
+    }
+}
+template <typename T, int RO, int R0, int N2, bool INV>
+__device__ __forceinline__ void comp_twiddles(cx<T> *a) {
+    if constexpr (N2 < R0) {
+        comp_twiddle_row<T, RO, R0, N2, 1, INV>(a);
+        comp_twiddles<T, RO, R0, N2 + 1, INV>(a);
+    }
+}
+
+template <typename T, int R, bool INV> __device__ __forceinline__ void dft(cx<T> *v);
+
+// In-register DFT of RC = RO * R0 values (RO in {3, 5, 9}, R0 a power of two),
+// natural order in and out, by one Cooley-Tukey step: with n = R0 n1 + n2 and
+// k = k1 + RO k2, X[k] = sum_n2 w_R0^{n2 k2} w_RC^{n2 k1} sum_n1 w_RO^{n1 k1} x[n].
+template <typename T, int RO, int R0, bool INV>
+__device__ __forceinline__ void dft_comp(cx<T> *x) {
+    if constexpr (R0 == 1) {
+        dft_odd<T, RO, INV>(x);
+    } else {
+        cx<T> a[RO * R0];  // a[n2 * RO + k1]
+#pragma unroll
+        for (int n2 = 0; n2 < R0; ++n2) {
+            cx<T> u[RO];
+#pragma unroll
+            for (int n1 = 0; n1 < RO; ++n1) u[n1] = x[R0 * n1 + n2];
+            dft_odd<T, RO, INV>(u);
+#pragma unroll
+            for (int k1 = 0; k1 < RO; ++k1) a[n2 * RO + k1] = u[k1];
+        }
+        comp_twiddles<T, RO, R0, 1, INV>(a);
+#pragma unroll
+        for (int k1 = 0; k1 < RO; ++k1) {
+            cx<T> w[R0];
+#pragma unroll
+            for (int n2 = 0; n2 < R0; ++n2) w[n2] = a[n2 * RO + k1];
+            dft<T, R0, INV>(w);
+#pragma unroll
+            for (int k2 = 0; k2 < R0; ++k2) x[k1 + RO * k2] = w[k2];
+        }
+    }
+}
+
 // Twiddle table pair for the length-L transform root w_L: w_L^e = hi[e >> B] * lo[e & (2^B-1)].
 // Complex roots are exp(-2*pi*i/L), computed in double precision on the host and rounded to T.
 template <typename T> struct TwTab {
@@ -285,6 +392,7 @@ constexpr uint32_t smem_elems() { return (uint32_t)LEN * COLS + ((uint32_t)LEN *
 // [E, ..., E, R0], so the forward's output distribution over threads equals
 // the inverse's input distribution and the two chain in registers.
 __host__ __device__ constexpr int odd_part(int v) { return (v & 1) ? v : odd_part(v >> 1); }
+constexpr int kMaxCompositeRadix = 24;
 __host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
 
 // Stage plan of a Stockham FFT of length LEN = RO * 2^k2 (RO odd: 1, 3, 5 or 9)
@@ -301,6 +409,11 @@ template <int LEN, int E> struct Plan {
     static constexpr int q = (k + e - 1) / e;  // power-of-two stages
     static constexpr int r0 = 1 << (k - (q - 1) * e);
     static constexpr int TC = LEN / E;  // threads per column
+    // The odd stage absorbs the radix-r0 stage when r0 < E and the composite radix
+    // RO * r0 stays within a register budget: stages [RO * r0], E, ..., E.
+    static constexpr bool FOLD = RO > 1 && r0 < E && RO * r0 <= kMaxCompositeRadix;
+    static constexpr int R0C = FOLD ? r0 : 1;  // power-of-two factor of the odd stage
+    static constexpr int RC = RO * R0C;        // radix of the odd stage
     static_assert(RO == 1 || RO == 3 || RO == 5 || RO == 9, "odd factor must be 1, 3, 5 or 9");
     static_assert(RO > 1 || q >= 2, "LEN must exceed E");
     static_assert((1 << k) == K2 && (1 << e) == E && K2 >= E, "power-of-two part must be >= E");
@@ -389,7 +502,9 @@ __device__ __forceinline__ void fwd_pow2(cx<T> *sm, cx<T> *v, uint32_t tq, uint3
 // from the first). The first stage's inputs are in registers. With TO_SMEM the
 // last stage writes its outputs to shared memory (an odd stage follows),
 // otherwise they stay in registers.
-template <typename T, int LEN, int COLS, int E, int S, int P0, bool TO_SMEM>
+// LAST is the index of the last power-of-two stage to run (q - 1, or q - 2 when
+// the odd stage absorbs the radix-r0 stage).
+template <typename T, int LEN, int COLS, int E, int S, int P0, bool TO_SMEM, int LAST = Plan<LEN, E>::q - 1>
 __device__ __forceinline__ void inv_pow2(cx<T> *sm, cx<T> *v, uint32_t tq, uint32_t col, const TwTab<T> &tw) {
     using PL = Plan<LEN, E>;
     constexpr int R = (S == PL::q - 1) ? PL::r0 : E;
@@ -397,12 +512,12 @@ __device__ __forceinline__ void inv_pow2(cx<T> *sm, cx<T> *v, uint32_t tq, uint3
         __syncthreads();
         load_from_smem<T, LEN, COLS, E, R>(sm, v, tq, col);
     }
-    if constexpr (S == PL::q - 1 && !TO_SMEM) {
+    if constexpr (S == LAST && !TO_SMEM) {
         stage_in_regs<T, LEN, COLS, E, R, P0, true>(v, tq, tw);
     } else {
         if constexpr (S > 0) __syncthreads();
         stage_to_smem<T, LEN, COLS, E, R, P0, true>(sm, v, tq, col, tw);
-        if constexpr (S < PL::q - 1) inv_pow2<T, LEN, COLS, E, S + 1, P0 * R, TO_SMEM>(sm, v, tq, col, tw);
+        if constexpr (S < LAST) inv_pow2<T, LEN, COLS, E, S + 1, P0 * R, TO_SMEM, LAST>(sm, v, tq, col, tw);
     }
 }
 
@@ -421,51 +536,64 @@ __device__ __forceinline__ void cta_fft(cx<T> *sm, cx<T> *v, uint32_t tq, uint32
     }
 }
 
-// Forward transform of a contiguous row of LEN = RO * 2^k elements (RO > 1):
-// the odd first stage reads its inputs through ld(index) and writes shared
-// memory; the power-of-two stages follow. Outputs end in registers (idx_e).
+// Forward transform of a contiguous row of LEN = RO * 2^k elements (RO > 1).
+// The first stage has the odd (or composite) radix RC = Plan::RC at span 1: group
+// g < LEN / RC reads elements g + r LEN / RC through ld(index), transforms, and
+// writes shared-memory slots g RC + r (odd_first_stage). The power-of-two stages
+// follow (fwd_odd_rest); outputs end in registers (idx_e).
 template <typename T, int LEN, int E, class Ld>
-__device__ __forceinline__ void cta_fft_fwd_odd(cx<T> *sm, cx<T> *v, uint32_t tq, const TwTab<T> &tw, Ld ld) {
+__device__ __forceinline__ void odd_first_stage(cx<T> *sm, uint32_t tq, Ld ld) {
     using PL = Plan<LEN, E>;
-    constexpr int RO = PL::RO, K2 = PL::K2, TC = PL::TC;
-    constexpr int G = (K2 + TC - 1) / TC;  // odd groups per thread (the last may be partial)
+    constexpr int RC = PL::RC, K = LEN / RC, TC = PL::TC;
+    constexpr int G = (K + TC - 1) / TC;  // groups per thread (the last may be partial)
 #pragma unroll
     for (int j = 0; j < G; ++j) {
         const uint32_t g = tq + (uint32_t)j * TC;
-        if (g < (uint32_t)K2) {
-            cx<T> u[RO];
+        if (g < (uint32_t)K) {
+            cx<T> u[RC];
 #pragma unroll
-            for (int r = 0; r < RO; ++r) u[r] = ld(g + (uint32_t)r * K2);
-            dft_odd<T, RO, false>(u);
+            for (int r = 0; r < RC; ++r) u[r] = ld(g + (uint32_t)r * K);
+            dft_comp<T, PL::RO, PL::R0C, false>(u);
 #pragma unroll
-            for (int r = 0; r < RO; ++r) sm[sidx<1>(g * RO + (uint32_t)r, 0)] = u[r];
+            for (int r = 0; r < RC; ++r) sm[sidx<1>(g * RC + (uint32_t)r, 0)] = u[r];
         }
     }
-    fwd_pow2<T, LEN, 1, E, 0, RO, false>(sm, v, tq, 0, tw);
+}
+
+template <typename T, int LEN, int E>
+__device__ __forceinline__ void fwd_odd_rest(cx<T> *sm, cx<T> *v, uint32_t tq, const TwTab<T> &tw) {
+    using PL = Plan<LEN, E>;
+    fwd_pow2<T, LEN, 1, E, PL::FOLD ? 1 : 0, PL::RC, false>(sm, v, tq, 0, tw);
+}
+
+template <typename T, int LEN, int E, class Ld>
+__device__ __forceinline__ void cta_fft_fwd_odd(cx<T> *sm, cx<T> *v, uint32_t tq, const TwTab<T> &tw, Ld ld) {
+    odd_first_stage<T, LEN, E>(sm, tq, ld);
+    fwd_odd_rest<T, LEN, E>(sm, v, tq, tw);
 }
 
 // Inverse transform of a row (RO > 1): power-of-two stages from registers
-// (idx_e layout) into shared memory, then the odd last stage, whose outputs go
-// through st(index, value).
+// (idx_e layout) into shared memory, then the odd (or composite) last stage at
+// span K = LEN / RC: group g < K reads slots g + r K, takes the twiddles
+// w_LEN^{-r g}, transforms, and its outputs go through st(g + r K, value).
 template <typename T, int LEN, int E, class St>
 __device__ __forceinline__ void cta_fft_inv_odd(cx<T> *sm, cx<T> *v, uint32_t tq, const TwTab<T> &tw, St st) {
     using PL = Plan<LEN, E>;
-    constexpr int RO = PL::RO, K2 = PL::K2, TC = PL::TC;
-    constexpr int G = (K2 + TC - 1) / TC;
-    inv_pow2<T, LEN, 1, E, 0, 1, true>(sm, v, tq, 0, tw);
+    constexpr int RC = PL::RC, K = LEN / RC, TC = PL::TC;
+    constexpr int G = (K + TC - 1) / TC;
+    inv_pow2<T, LEN, 1, E, 0, 1, true, PL::FOLD ? PL::q - 2 : PL::q - 1>(sm, v, tq, 0, tw);
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < G; ++j) {
         const uint32_t g = tq + (uint32_t)j * TC;
-        if (g < (uint32_t)K2) {
-            cx<T> u[RO];
+        if (g < (uint32_t)K) {
+            cx<T> u[RC];
 #pragma unroll
-            for (int r = 0; r < RO; ++r) u[r] = sm[sidx<1>(g + (uint32_t)r * K2, 0)];
-            // span K2: twiddle w_LEN^{r g}
-            stage_twiddles<T, true, RO>(u, tw, g * (tw.F / LEN));
-            dft_odd<T, RO, true>(u);
+            for (int r = 0; r < RC; ++r) u[r] = sm[sidx<1>(g + (uint32_t)r * K, 0)];
+            stage_twiddles<T, true, RC>(u, tw, g * (tw.F / LEN));
+            dft_comp<T, PL::RO, PL::R0C, true>(u);
 #pragma unroll
-            for (int r = 0; r < RO; ++r) st(g + (uint32_t)r * K2, u[r]);
+            for (int r = 0; r < RC; ++r) st(g + (uint32_t)r * K, u[r]);
         }
     }
 }

@@ -4,10 +4,12 @@
 // two >= n+m-1 (paper Section 2.2: the FFT length of the standard Toeplitz
 // hash is n+r-1), split into two or three passes (paper Algorithm 1 splits a
 // long FFT into short row and column FFTs with a twiddle step in between).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -55,6 +57,17 @@ inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 
 
 }  // namespace
 
+// The arguments of an issued batch, kept for its guard step.
+struct PendingBatch {
+    bool active = false;
+    const uint64_t *keys = nullptr;
+    uint32_t nkeys = 0;
+    uint64_t kstride = 0;
+    uint64_t *out = nullptr;
+    uint64_t ostride = 0;
+    pa_stream_t stream = nullptr;
+};
+
 struct pa_plan {
     uint64_t n = 0, m = 0;
     pa_dtype_t dtype = PA_FP64;
@@ -70,13 +83,16 @@ struct pa_plan {
     uint32_t max_chunk_pairs = 1;
     uint32_t *popc = nullptr;    // per key
     uint32_t *marg = nullptr;    // per key, float bits
+    uint32_t *err = nullptr;     // device word: bit 0 = a bounded copy wait ran out of time
     uint32_t key_cap = 0;
-    float *h_marg = nullptr;     // pinned
+    float *h_marg = nullptr;     // pinned: h_cap margins, then the error word
     uint32_t h_cap = 0;
     uint64_t *seed_copy = nullptr;  // the seed bits, kept for an escalation plan
     bool seeded = false;
     float guard = 0.25f;
     pa_plan_t *fallback = nullptr;    // next-wider plan (FP32 -> FP64 -> NTT64) for keys that fail the guard
+    PendingBatch pending;             // a batch issued by pa_hash_batch_async, not yet finished
+    cudaEvent_t done = nullptr;       // recorded behind the margins' read-back
     std::mutex mu;
     // kernel timing
     bool prof = false;
@@ -284,7 +300,7 @@ int ensure_host(pa_plan_t *p, uint32_t nkeys) {
     if (p->h_marg) cudaFreeHost(p->h_marg);
     p->h_marg = nullptr;
     p->h_cap = 0;
-    PA_CUDA(cudaMallocHost(&p->h_marg, (size_t)nkeys * sizeof(float)));
+    PA_CUDA(cudaMallocHost(&p->h_marg, ((size_t)nkeys + 1) * sizeof(float)));
     p->h_cap = nkeys;
     return PA_OK;
 }
@@ -339,11 +355,11 @@ int run_keys(pa_plan_t *p, const uint64_t *keys, uint32_t nkeys, uint64_t kstrid
         { Timed t_(p, K_FWD_KEYS, st); PA_CUDA(launch_fwd_keys<T>(g.lg1, kp, nk, kstride, p->n, W, p->L, pairs, tw, st)); }
         if (g.lgM) {
             { Timed t_(p, K_MID_FWD, st); PA_CUDA(launch_mid<T>(g.lgM, false, W, p->L, g.inner(), pairs, tw, st)); }
-            { Timed t_(p, K_MIDDLE_CONV, st); PA_CUDA(launch_middle<T>(g.ro, g.lgI, 0, W, spec, p->L, pairs, tw, one<T>(), st)); }
+            { Timed t_(p, K_MIDDLE_CONV, st); PA_CUDA(launch_middle<T>(g.ro, g.lgI, 0, W, spec, p->L, pairs, tw, one<T>(), st, p->err)); }
             { Timed t_(p, K_MID_INV, st); PA_CUDA(launch_mid<T>(g.lgM, true, W, p->L, g.inner(), pairs, tw, st)); }
         } else {
             Timed t_(p, K_MIDDLE_CONV, st);
-            PA_CUDA(launch_middle<T>(g.ro, g.lgI, 0, W, spec, p->L, pairs, tw, one<T>(), st));
+            PA_CUDA(launch_middle<T>(g.ro, g.lgI, 0, W, spec, p->L, pairs, tw, one<T>(), st, p->err));
         }
         { Timed t_(p, K_INV_BITS, st); PA_CUDA(launch_inv_bits<T>(g.lg1, W, p->L, p->m, nk, popc + k0, marg + k0, op, ostride, pairs, tw, st)); }
     }
@@ -360,11 +376,208 @@ void free_plan(pa_plan_t *p) {
     cudaFree(p->work);
     cudaFree(p->popc);
     cudaFree(p->marg);
+    cudaFree(p->err);
     cudaFree(p->seed_copy);
     if (p->h_marg) cudaFreeHost(p->h_marg);
+    if (p->done) cudaEventDestroy(p->done);
     for (cudaEvent_t e : p->ev_a) cudaEventDestroy(e);
     for (cudaEvent_t e : p->ev_b) cudaEventDestroy(e);
     delete p;
+}
+
+bool plan_args_ok(uint64_t n, uint64_t m, pa_dtype_t dtype) {
+    if (n == 0 || m == 0 || m > n || n > (1ull << 27)) return false;
+    return dtype == PA_FP64 || dtype == PA_FP32_GUARD || dtype == PA_NTT64;
+}
+
+// Pass lengths of a split as the ABI reports them: L1, then the middle strided pass
+// and the innermost pass for three passes, else the innermost pass and 1.
+void split_lengths(const Geometry &g, uint32_t *L1, uint32_t *L2, uint32_t *L3) {
+    *L1 = 1u << g.lg1;
+    *L2 = g.lgM ? (1u << g.lgM) : g.inner();
+    *L3 = g.lgM ? g.inner() : 1u;
+}
+
+int build_plan_twiddles(pa_plan_t *p) {
+    return (p->dtype == PA_FP32_GUARD) ? build_twiddles<float>(p)
+           : (p->dtype == PA_FP64)     ? build_twiddles<double>(p)
+                                       : build_twiddles<Zp>(p);
+}
+
+void free_plan_twiddles(pa_plan_t *p) {
+    cudaFree(p->tw_hi);
+    cudaFree(p->tw_lo);
+    cudaFree(p->tw_fine);
+    p->tw_hi = p->tw_lo = p->tw_fine = nullptr;
+}
+
+// ---- split autotuner ---------------------------------------------------------------------------
+// Every valid split of a transform length runs the same arithmetic in a different
+// pass structure; which one is fastest depends on the kernel instances and is
+// measured, not modelled: once per (L, dtype) and process, each candidate hashes a
+// batch of all-zero keys (the kernels' cost does not depend on the bit values)
+// and the fastest is kept. PA_PLAN_TUNE=0 turns it off (the default split is used).
+std::mutex g_split_mu;
+std::map<std::pair<uint64_t, int>, Geometry> g_split;
+
+bool tuning_enabled() {
+    const char *s = std::getenv("PA_PLAN_TUNE");
+    return !(s && s[0] == '0');
+}
+
+// Median of five timed runs after one warm-up run (which also loads the kernels).
+template <typename T>
+int time_split(pa_plan_t *p, uint32_t nkeys, const uint64_t *keys, uint64_t kw, uint64_t *out, uint64_t ow,
+               cudaStream_t st, cudaEvent_t a, cudaEvent_t b, float *ms) {
+    float t[6] = {};
+    for (int rep = 0; rep < 6; ++rep) {
+        PA_CUDA(cudaEventRecord(a, st));
+        int rc = run_keys<T>(p, keys, nkeys, kw, out, ow, p->popc, p->marg, st);
+        if (rc != PA_OK) return rc;
+        PA_CUDA(cudaEventRecord(b, st));
+        PA_CUDA(cudaEventSynchronize(b));
+        PA_CUDA(cudaEventElapsedTime(&t[rep], a, b));
+    }
+    std::sort(t + 1, t + 6);
+    *ms = t[3];
+    return PA_OK;
+}
+
+// Chooses p->geo among the candidates of p->L (cached per process). The plan's spectrum
+// slot must exist; twiddles and work buffers made for the trials are released again.
+int tune_split(pa_plan_t *p, const std::vector<Geometry> &cand) {
+    const std::pair<uint64_t, int> key{p->L, (int)p->dtype};
+    {
+        std::lock_guard<std::mutex> lk(g_split_mu);
+        auto it = g_split.find(key);
+        if (it != g_split.end()) {
+            p->geo = it->second;
+            return PA_OK;
+        }
+    }
+    const size_t per_pair = (size_t)p->L * elem_bytes(p->dtype);
+    uint32_t pairs = (uint32_t)(((size_t)512 << 20) / per_pair);  // about 512 MB of work: well past the L2
+    if (pairs < 1) pairs = 1;
+    if (pairs > 32) pairs = 32;
+    if (pairs > p->max_chunk_pairs) pairs = p->max_chunk_pairs;
+    const uint32_t nkeys = 2 * pairs;
+    const uint64_t kw = ((p->n + 63) / 64 + 1) & ~1ull, ow = ((p->m + 63) / 64 + 1) & ~1ull;
+    uint64_t *keys = nullptr, *out = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    int rc = PA_OK;
+    float best = 0.f;
+    Geometry bestg = p->geo;
+    auto fail = [&](int r) {
+        cudaFree(keys);
+        cudaFree(out);
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+        if (st) cudaStreamDestroy(st);
+        return r;
+    };
+    cudaError_t e = cudaMalloc(&keys, (size_t)nkeys * kw * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&out, (size_t)nkeys * ow * 8);
+    if (e == cudaSuccess) e = cudaMemset(keys, 0, (size_t)nkeys * kw * 8);
+    if (e == cudaSuccess) e = cudaMemset(p->spec, 0, per_pair);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(PA_ENOMEM);
+    }
+    if (e != cudaSuccess) return fail(cuda_fail(e, "split autotuner set-up"));
+    if ((rc = ensure_work(p, pairs)) != PA_OK || (rc = ensure_keys(p, nkeys)) != PA_OK) return fail(rc);
+    for (size_t i = 0; i < cand.size(); ++i) {
+        p->geo = cand[i];
+        if ((rc = build_plan_twiddles(p)) != PA_OK) return fail(rc);
+        float ms = 0.f;
+        rc = (p->dtype == PA_FP32_GUARD) ? time_split<float>(p, nkeys, keys, kw, out, ow, st, a, b, &ms)
+             : (p->dtype == PA_FP64)     ? time_split<double>(p, nkeys, keys, kw, out, ow, st, a, b, &ms)
+                                         : time_split<Zp>(p, nkeys, keys, kw, out, ow, st, a, b, &ms);
+        free_plan_twiddles(p);
+        if (rc != PA_OK) return fail(rc);
+        if (i == 0 || ms < best) {
+            best = ms;
+            bestg = cand[i];
+        }
+    }
+    p->geo = bestg;
+    // The trial work buffer is sized for the trials, not for this plan's batches.
+    cudaFree(p->work);
+    p->work = nullptr;
+    p->work_pairs = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_split_mu);
+        g_split[key] = bestg;
+    }
+    return fail(PA_OK);
+}
+
+// pa_plan, with the split forced when `force` is given.
+int plan_create(uint64_t n, uint64_t m, pa_dtype_t dtype, const Geometry *force, pa_plan_t **out) {
+    if (!out) return PA_EINVAL;
+    *out = nullptr;
+    if (!plan_args_ok(n, m, dtype)) return PA_EINVAL;
+    pa_plan_t *p = new pa_plan_t();
+    p->n = n;
+    p->m = m;
+    p->dtype = dtype;
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        delete p;
+        return cuda_fail(cudaGetLastError(), "cudaGetDevice");
+    }
+    const Geometry geo = force ? *force : choose_geometry(n + m - 1, dtype, false);
+    if (geo.L == 0) {
+        delete p;
+        return PA_EUNSUPPORTED;
+    }
+    p->L = geo.L;
+    p->geo = geo;
+    cudaError_t e = cudaMalloc(&p->spec, (size_t)p->L * elem_bytes(dtype));
+    if (e == cudaSuccess) e = cudaMalloc(&p->err, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(p->err, 0, sizeof(uint32_t));
+    if (e != cudaSuccess) {
+        free_plan(p);
+        if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();
+            return PA_ENOMEM;
+        }
+        return cuda_fail(e, "cudaMalloc(spec)");
+    }
+    p->max_chunk_pairs = chunk_pairs_limit(p);
+    int rc = PA_OK;
+    if (!force && tuning_enabled()) {
+        const std::vector<Geometry> cand = geometry_candidates(p->L, dtype, false);
+        if (cand.size() > 1) rc = tune_split(p, cand);
+    }
+    if (rc == PA_OK) rc = build_plan_twiddles(p);
+    if (rc != PA_OK) {
+        free_plan(p);
+        return rc;
+    }
+    p->max_chunk_pairs = chunk_pairs_limit(p);  // depends on the split
+    *out = p;
+    return PA_OK;
+}
+
+// Recomputes key k of a finished batch with the plan's fallback (one mode wider), in
+// stream order on the batch's stream, and reports the margin and mode that produced it.
+int escalate_key(pa_plan_t *p, const PendingBatch &b, uint32_t k, float *margin, int32_t *mode) {
+    if (!p->fallback->seeded) {
+        int rc = pa_set_seed(p->fallback, p->seed_copy, p->n + p->m - 1, b.stream);
+        if (rc != PA_OK) return rc;
+    }
+    float m2 = 0.f;
+    int32_t mode2 = 0;
+    pa_batch_info_t sub{&m2, &mode2, 0, 0};
+    int rc = pa_hash_batch(p->fallback, b.keys + (uint64_t)k * b.kstride, 1, b.kstride, b.out + (uint64_t)k * b.ostride,
+                           b.ostride, b.stream, &sub);
+    if (rc != PA_OK) return rc;
+    *margin = m2;
+    *mode = mode2;
+    return PA_OK;
 }
 
 }  // namespace
@@ -396,45 +609,38 @@ const char *pa_strerror(int code) {
 const char *pa_last_cuda_error(void) { return g_last_cuda_error.c_str(); }
 
 int pa_plan(uint64_t n, uint64_t m, pa_dtype_t dtype, pa_plan_t **out) {
+    return plan_create(n, m, dtype, nullptr, out);
+}
+
+int pa_plan_splits(uint64_t n, uint64_t m, pa_dtype_t dtype, uint32_t *L1, uint32_t *L2, uint32_t *L3, int cap,
+                   int *count) {
+    if (!count || cap < 0 || (cap > 0 && (!L1 || !L2 || !L3))) return PA_EINVAL;
+    *count = 0;
+    if (!plan_args_ok(n, m, dtype)) return PA_EINVAL;
+    const Geometry geo = choose_geometry(n + m - 1, dtype, false);
+    if (geo.L == 0) return PA_EUNSUPPORTED;
+    const std::vector<Geometry> cand = geometry_candidates(geo.L, dtype, false);
+    int c = 0;
+    for (const Geometry &g : cand) {
+        if (c < cap) split_lengths(g, &L1[c], &L2[c], &L3[c]);
+        ++c;
+    }
+    *count = c;
+    return PA_OK;
+}
+
+int pa_plan_split(uint64_t n, uint64_t m, pa_dtype_t dtype, uint32_t L1, uint32_t L2, uint32_t L3, pa_plan_t **out) {
     if (!out) return PA_EINVAL;
     *out = nullptr;
-    if (n == 0 || m == 0 || m > n || n > (1ull << 27)) return PA_EINVAL;
-    if (dtype != PA_FP64 && dtype != PA_FP32_GUARD && dtype != PA_NTT64) return PA_EINVAL;
-    pa_plan_t *p = new pa_plan_t();
-    p->n = n;
-    p->m = m;
-    p->dtype = dtype;
-    if (cudaGetDevice(&p->device) != cudaSuccess) {
-        delete p;
-        return cuda_fail(cudaGetLastError(), "cudaGetDevice");
+    if (!plan_args_ok(n, m, dtype)) return PA_EINVAL;
+    const Geometry geo = choose_geometry(n + m - 1, dtype, false);
+    if (geo.L == 0) return PA_EUNSUPPORTED;
+    for (const Geometry &g : geometry_candidates(geo.L, dtype, false)) {
+        uint32_t a, b, c;
+        split_lengths(g, &a, &b, &c);
+        if (a == L1 && b == L2 && c == L3) return plan_create(n, m, dtype, &g, out);
     }
-    const uint64_t need = n + m - 1;
-    const Geometry geo = choose_geometry(need, dtype, false);
-    if (geo.L == 0) {
-        delete p;
-        return PA_EUNSUPPORTED;
-    }
-    p->L = geo.L;
-    p->geo = geo;
-    int rc = (dtype == PA_FP32_GUARD) ? build_twiddles<float>(p)
-             : (dtype == PA_FP64)     ? build_twiddles<double>(p)
-                                      : build_twiddles<Zp>(p);
-    if (rc != PA_OK) {
-        free_plan(p);
-        return rc;
-    }
-    cudaError_t e = cudaMalloc(&p->spec, (size_t)p->L * elem_bytes(dtype));
-    if (e != cudaSuccess) {
-        free_plan(p);
-        if (e == cudaErrorMemoryAllocation) {
-            cudaGetLastError();
-            return PA_ENOMEM;
-        }
-        return cuda_fail(e, "cudaMalloc(spec)");
-    }
-    p->max_chunk_pairs = chunk_pairs_limit(p);
-    *out = p;
-    return PA_OK;
+    return PA_EINVAL;
 }
 
 int pa_plan_destroy(pa_plan_t *plan) {
@@ -448,9 +654,11 @@ int pa_plan_destroy(pa_plan_t *plan) {
 int pa_plan_shape(const pa_plan_t *p, uint64_t *L, uint32_t *L1, uint32_t *L2, uint32_t *L3) {
     if (!p) return PA_EINVAL;
     if (L) *L = p->L;
-    if (L1) *L1 = 1u << p->geo.lg1;
-    if (L2) *L2 = p->geo.lgM ? (1u << p->geo.lgM) : p->geo.inner();
-    if (L3) *L3 = p->geo.lgM ? p->geo.inner() : 1u;
+    uint32_t a, b, c;
+    split_lengths(p->geo, &a, &b, &c);
+    if (L1) *L1 = a;
+    if (L2) *L2 = b;
+    if (L3) *L3 = c;
     return PA_OK;
 }
 
@@ -508,14 +716,15 @@ int pa_set_seed(pa_plan_t *p, const uint64_t *seed_dev, uint64_t seed_bits, pa_s
     return PA_OK;
 }
 
-int pa_hash_batch(pa_plan_t *p, const uint64_t *keys_dev, uint32_t nkeys, uint64_t key_stride_words,
-                  uint64_t *out_dev, uint64_t out_stride_words, pa_stream_t stream, pa_batch_info_t *info) {
+int pa_hash_batch_async(pa_plan_t *p, const uint64_t *keys_dev, uint32_t nkeys, uint64_t key_stride_words,
+                        uint64_t *out_dev, uint64_t out_stride_words, pa_stream_t stream) {
     if (!p || !keys_dev || !out_dev || nkeys == 0) return PA_EINVAL;
     if (!aligned16(keys_dev) || !aligned16(out_dev)) return PA_EINVAL;
     if (key_stride_words < (p->n + 63) / 64 || out_stride_words < (p->m + 63) / 64) return PA_EINVAL;
     if ((nkeys > 1 && (key_stride_words & 1)) || (nkeys > 1 && (out_stride_words & 1))) return PA_EINVAL;
     if (!p->seeded) return PA_ENOSEED;
     std::lock_guard<std::mutex> lk(p->mu);
+    if (p->pending.active) return PA_EAGAIN;
     DeviceGuard g(p->device);
     if (!g.ok) return cuda_fail(cudaGetLastError(), "cudaSetDevice");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -525,6 +734,9 @@ int pa_hash_batch(pa_plan_t *p, const uint64_t *keys_dev, uint32_t nkeys, uint64
     if (rc != PA_OK) return rc;
     rc = ensure_keys(p, nkeys);
     if (rc != PA_OK) return rc;
+    rc = ensure_host(p, nkeys);
+    if (rc != PA_OK) return rc;
+    if (!p->done) PA_CUDA(cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming));
     if (p->dtype == PA_FP32_GUARD)
         rc = run_keys<float>(p, keys_dev, nkeys, key_stride_words, out_dev, out_stride_words, p->popc, p->marg, st);
     else if (p->dtype == PA_FP64)
@@ -532,38 +744,55 @@ int pa_hash_batch(pa_plan_t *p, const uint64_t *keys_dev, uint32_t nkeys, uint64
     else
         rc = run_keys<Zp>(p, keys_dev, nkeys, key_stride_words, out_dev, out_stride_words, p->popc, p->marg, st);
     if (rc != PA_OK) return rc;
-    if (info) info->escalated = 0;
-    const bool need_margins = (p->dtype == PA_FP32_GUARD) || info != nullptr;
-    if (!need_margins) return PA_OK;
-
-    rc = ensure_host(p, nkeys);
-    if (rc != PA_OK) return rc;
+    // the margins and the error word travel back behind the kernels; pa_batch_finish waits for them
     PA_CUDA(cudaMemcpyAsync(p->h_marg, p->marg, (size_t)nkeys * sizeof(float), cudaMemcpyDeviceToHost, st));
-    PA_CUDA(cudaStreamSynchronize(st));
+    PA_CUDA(cudaMemcpyAsync(p->h_marg + nkeys, p->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    PA_CUDA(cudaEventRecord(p->done, st));
+    p->pending = PendingBatch{true, keys_dev, nkeys, key_stride_words, out_dev, out_stride_words, stream};
+    return PA_OK;
+}
+
+int pa_batch_finish(pa_plan_t *p, pa_batch_info_t *info) {
+    if (!p) return PA_EINVAL;
+    std::unique_lock<std::mutex> lk(p->mu);
+    if (!p->pending.active) return PA_EINVAL;
+    const PendingBatch b = p->pending;
+    p->pending.active = false;
+    DeviceGuard g(p->device);
+    if (!g.ok) return cuda_fail(cudaGetLastError(), "cudaSetDevice");
+    PA_CUDA(cudaEventSynchronize(p->done));
+    uint32_t err_word = 0;
+    std::memcpy(&err_word, p->h_marg + b.nkeys, sizeof(uint32_t));
+    if (err_word != 0) {
+        PA_CUDA(cudaMemset(p->err, 0, sizeof(uint32_t)));
+        return PA_ETIMEOUT;  // a bounded device wait ran out: this batch's outputs are not valid
+    }
+    if (info) info->escalated = 0;
     uint32_t escalated = 0;
-    for (uint32_t k = 0; k < nkeys; ++k) {
+    for (uint32_t k = 0; k < b.nkeys; ++k) {
         float mk_ = p->h_marg[k];
         int32_t mode = (int32_t)p->dtype;
-        if (p->dtype != PA_NTT64 && !(mk_ <= p->guard)) {
-            // Recompute this key one mode wider (the guard's escalation): FP32 -> FP64 -> exact NTT.
+        if (p->dtype == PA_FP32_GUARD && !(mk_ <= p->guard)) {
+            // Recompute this key one mode wider (the guard's escalation): FP32 -> FP64 (-> exact NTT
+            // inside the FP64 plan when its own margin fails).
             if (!p->fallback) {
                 pa_plan_t *fb = nullptr;
-                rc = pa_plan(p->n, p->m, p->dtype == PA_FP32_GUARD ? PA_FP64 : PA_NTT64, &fb);
+                int rc = pa_plan(p->n, p->m, PA_FP64, &fb);
                 if (rc != PA_OK) return rc;
                 p->fallback = fb;
             }
-            if (!p->fallback->seeded) {
-                rc = pa_set_seed(p->fallback, p->seed_copy, p->n + p->m - 1, stream);
-                if (rc != PA_OK) return rc;
-            }
-            float m2 = 0.f;
-            int32_t mode2 = 0;
-            pa_batch_info_t sub{&m2, &mode2, 0, 0};
-            rc = pa_hash_batch(p->fallback, keys_dev + (uint64_t)k * key_stride_words, 1, key_stride_words,
-                               out_dev + (uint64_t)k * out_stride_words, out_stride_words, stream, &sub);
+            int rc = escalate_key(p, b, k, &mk_, &mode);
             if (rc != PA_OK) return rc;
-            mk_ = m2;
-            mode = mode2;
+            ++escalated;
+        } else if (p->dtype == PA_FP64 && !(mk_ <= p->guard)) {
+            if (!p->fallback) {
+                pa_plan_t *fb = nullptr;
+                int rc = pa_plan(p->n, p->m, PA_NTT64, &fb);
+                if (rc != PA_OK) return rc;
+                p->fallback = fb;
+            }
+            int rc = escalate_key(p, b, k, &mk_, &mode);
+            if (rc != PA_OK) return rc;
             ++escalated;
         }
         if (info && info->margin) info->margin[k] = mk_;
@@ -571,6 +800,21 @@ int pa_hash_batch(pa_plan_t *p, const uint64_t *keys_dev, uint32_t nkeys, uint64
     }
     if (info) info->escalated = escalated;
     return PA_OK;
+}
+
+int pa_hash_batch(pa_plan_t *p, const uint64_t *keys_dev, uint32_t nkeys, uint64_t key_stride_words,
+                  uint64_t *out_dev, uint64_t out_stride_words, pa_stream_t stream, pa_batch_info_t *info) {
+    int rc = pa_hash_batch_async(p, keys_dev, nkeys, key_stride_words, out_dev, out_stride_words, stream);
+    if (rc != PA_OK) return rc;
+    const bool need_margins = (p->dtype == PA_FP32_GUARD) || info != nullptr;
+    if (!need_margins) {
+        // FP64 and NTT64 without diagnostics return right after issuing: the batch completes in
+        // stream order, and the error word is examined by the next call that waits.
+        std::lock_guard<std::mutex> lk(p->mu);
+        p->pending.active = false;
+        return PA_OK;
+    }
+    return pa_batch_finish(p, info);
 }
 
 }  // extern "C"

@@ -27,6 +27,7 @@
 // the 0.5 cliff (the precision concern of the paper's Section 5).
 #pragma once
 
+#include "bulk.cuh"
 #include "fft_core.cuh"
 
 namespace pa {
@@ -259,6 +260,110 @@ __global__ void __launch_bounds__(LEN / E, min_blocks_inner(LEN / E))
         for (int s = 0; s < E; ++s) w[idx_r0<LEN, E>(tq, s)] = v[s];
     } else {
         cta_fft_inv_odd<T, LEN, E>(sm, v, tq, tw, [&](uint32_t i, cx<T> x) { w[i] = x; });
+    }
+}
+
+// The fused convolution step (MODE 0 of k_middle) as a persistent, pipelined
+// kernel: each CTA owns a contiguous run of tiles (tile t = row t / pairs of
+// pair t % pairs, so consecutive tiles share a seed-spectrum row) and keeps two
+// staging rows in shared memory, filled by bulk asynchronous copies: the input
+// row of the next tile is copied while the current tile is transformed, and the
+// seed-spectrum row is copied only when the row changes. The arithmetic is
+// k_middle's, step for step. A copy wait that runs out of time sets bit 0 of
+// *err and the CTA returns (after a bounded wait for its copies in flight).
+template <typename T, int LEN, int E>
+__global__ void __launch_bounds__(LEN / E, min_blocks_inner(LEN / E))
+    k_middle_pipe(cx<T> *__restrict__ W, const cx<T> *__restrict__ spec, uint64_t L, uint32_t pairs,
+                  uint32_t tiles_per_cta, TwTab<T> tw, uint32_t *__restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    constexpr uint32_t kRowBytes = LEN * sizeof(cx<T>);
+    static_assert(kRowBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
+    cx<T> *stg = reinterpret_cast<cx<T> *>(smem_raw);  // staged input row
+    cx<T> *ssp = stg + LEN;                              // staged seed-spectrum row
+    cx<T> *sm = ssp + LEN;                               // exchange buffer of the transform
+    __shared__ __align__(8) uint64_t bar[2];             // [0]: input row, [1]: spectrum row
+    const uint32_t tq = threadIdx.x;
+    const uint32_t ntiles = (uint32_t)(L / LEN) * pairs;
+    const uint32_t t0 = blockIdx.x * tiles_per_cta;
+    const uint32_t t1 = (t0 + tiles_per_cta < ntiles) ? t0 + tiles_per_cta : ntiles;
+    if (t0 >= t1) return;
+    auto row_of = [&](uint32_t t) { return W + (uint64_t)(t % pairs) * L + (uint64_t)(t / pairs) * LEN; };
+    uint32_t srow = t0 / pairs;  // spectrum row staged (or in flight) in ssp
+    if (tq == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init_fence();
+        mbar_arrive_expect_tx(&bar[0], kRowBytes);
+        bulk_load(stg, row_of(t0), kRowBytes, &bar[0]);
+        mbar_arrive_expect_tx(&bar[1], kRowBytes);
+        bulk_load(ssp, spec + (uint64_t)srow * LEN, kRowBytes, &bar[1]);
+    }
+    __syncthreads();
+    uint32_t pd = 0, ps = 0;
+    bool spec_wait = true;
+    for (uint32_t t = t0; t < t1; ++t) {
+        const uint32_t row = t / pairs;
+        if (row != srow) {
+            // every thread finished reading ssp before the barrier that closed the last tile
+            if (tq == 0) {
+                mbar_arrive_expect_tx(&bar[1], kRowBytes);
+                bulk_load(ssp, spec + (uint64_t)row * LEN, kRowBytes, &bar[1]);
+            }
+            srow = row;
+            spec_wait = true;
+        }
+        bool ok = mbar_wait(&bar[0], pd);
+        pd ^= 1u;
+        if (!__syncthreads_and(ok)) {
+            if (tq == 0) {  // record the failure, then give the copies in flight a bounded wait
+                atomicOr(err, 1u);
+                mbar_wait(&bar[0], pd ^ 1u);
+                if (spec_wait) mbar_wait(&bar[1], ps);
+            }
+            return;
+        }
+        cx<T> v[E];
+        if constexpr (Plan<LEN, E>::RO == 1) {
+#pragma unroll
+            for (int s = 0; s < E; ++s) v[s] = stg[idx_r0<LEN, E>(tq, s)];
+        } else {
+            odd_first_stage<T, LEN, E>(sm, tq, [&](uint32_t i) { return stg[i]; });
+        }
+        __syncthreads();  // stg has been read: refill it with the next tile's row
+        if (tq == 0 && t + 1 < t1) {
+            mbar_arrive_expect_tx(&bar[0], kRowBytes);
+            bulk_load(stg, row_of(t + 1), kRowBytes, &bar[0]);
+        }
+        if constexpr (Plan<LEN, E>::RO == 1) {
+            cta_fft<T, LEN, 1, E, false>(sm, v, tq, 0, tw);
+        } else {
+            fwd_odd_rest<T, LEN, E>(sm, v, tq, tw);
+        }
+        if (spec_wait) {
+            ok = mbar_wait(&bar[1], ps);
+            ps ^= 1u;
+            spec_wait = false;
+            if (!__syncthreads_and(ok)) {
+                if (tq == 0) {
+                    atomicOr(err, 1u);
+                    mbar_wait(&bar[1], ps ^ 1u);
+                    if (t + 1 < t1) mbar_wait(&bar[0], pd);
+                }
+                return;
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < E; ++s) v[s] = Arith<T>::mul(v[s], ssp[idx_e<LEN, E>(tq, s)]);
+        __syncthreads();  // the forward transform's last shared-memory reads are done
+        cx<T> *w = row_of(t);
+        if constexpr (Plan<LEN, E>::RO == 1) {
+            cta_fft<T, LEN, 1, E, true>(sm, v, tq, 0, tw);
+#pragma unroll
+            for (int s = 0; s < E; ++s) w[idx_r0<LEN, E>(tq, s)] = v[s];
+        } else {
+            cta_fft_inv_odd<T, LEN, E>(sm, v, tq, tw, [&](uint32_t i, cx<T> x) { w[i] = x; });
+        }
+        __syncthreads();  // sm and ssp are free for the next tile
     }
 }
 

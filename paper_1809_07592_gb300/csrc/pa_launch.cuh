@@ -99,12 +99,66 @@ cudaError_t launch_mid(int lgLEN, bool inverse, cx<T> *W, uint64_t L, uint32_t S
     });
 }
 
+// Shared memory of k_middle_pipe: two staging rows and the exchange buffer. The
+// pipelined kernel is used for rows of at least 3072 elements where that leaves
+// room for two CTAs per SM; on shorter rows the per-tile barriers and the extra
+// shared-memory traffic of the staging cost more than the hidden load latency
+// saves (measured: 1152-2560 slower or even, 3072-4608 faster by 6-13 %).
+template <typename T, int LEN>
+constexpr size_t pipe_smem_bytes() {
+    return 2 * (size_t)LEN * sizeof(cx<T>) + smem_bytes<T, LEN, 1>();
+}
+template <typename T, int LEN>
+constexpr bool pipe_ok() {
+    return LEN >= 3072 && pipe_smem_bytes<T, LEN>() <= 112 * 1024;
+}
+
+// Persistent grid of k_middle_pipe: resident CTAs per SM (occupancy query) times the
+// SM count, each CTA owning an equal run of tiles. `cache` (one per kernel instance)
+// keeps the product per device.
+template <typename K>
+cudaError_t persistent_ctas(K kern, int threads, size_t smem, int *cache, uint32_t *ctas) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 16) return cudaErrorInvalidDevice;
+    if (cache[dev] == 0) {
+        int o = 0, n = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, threads, smem);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        if (o < 1) o = 1;
+        cache[dev] = o * n;
+    }
+    *ctas = (uint32_t)cache[dev];
+    return cudaSuccess;
+}
+
 template <typename T, int LEN>
 cudaError_t middle_at(int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pairs, TwTab<T> tw, cx<T> scale,
-                      cudaStream_t st) {
+                      cudaStream_t st, uint32_t *err) {
     constexpr int E = Shape<T>::E;
     constexpr size_t sb = smem_bytes<T, LEN, 1>();
     dim3 grid((unsigned)(L / LEN), pairs);
+    if constexpr (pipe_ok<T, LEN>()) {
+        if (mode == 0 && err != nullptr) {
+            auto kern = k_middle_pipe<T, LEN, E>;
+            constexpr size_t pb = pipe_smem_bytes<T, LEN>();
+            cudaError_t e = set_smem(kern, pb);
+            if (e != cudaSuccess) return e;
+            static int cache[16] = {0};  // per (T, LEN): resident CTAs on each device
+            uint32_t ctas = 0;
+            e = persistent_ctas(kern, LEN / E, pb, cache, &ctas);
+            if (e != cudaSuccess) return e;
+            const uint64_t ntiles = (L / LEN) * pairs;
+            if (ntiles > 0xFFFFFFFFull) return cudaErrorInvalidValue;
+            const uint32_t per = (uint32_t)((ntiles + ctas - 1) / ctas);
+            const uint32_t nct = (uint32_t)((ntiles + per - 1) / per);
+            kern<<<nct, LEN / E, pb, st>>>(W, spec, L, pairs, per, tw, err);
+            return cudaGetLastError();
+        }
+    }
     if (mode == 0) {
         auto kern = k_middle<T, LEN, E, 0>;
         cudaError_t e = set_smem(kern, sb);
@@ -121,18 +175,18 @@ cudaError_t middle_at(int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pair
 
 template <typename T>
 cudaError_t launch_middle(int ro, int lg, int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pairs, TwTab<T> tw,
-                          cx<T> scale, cudaStream_t st) {
+                          cx<T> scale, cudaStream_t st, uint32_t *err) {
     if (ro == 1) {
         return by_len<kMinLgMiddle, MaxLgMiddle<T>::v>(lg, [&](auto c) {
-            return middle_at<T, decltype(c)::value>(mode, W, spec, L, pairs, tw, scale, st);
+            return middle_at<T, decltype(c)::value>(mode, W, spec, L, pairs, tw, scale, st, err);
         });
     }
     if constexpr (std::is_same<T, Zp>::value) {
         return cudaErrorInvalidValue;  // the exact transform keeps power-of-two lengths
     } else {
-        if (ro == 3) return launch_middle_odd<T, 3>(lg, mode, W, spec, L, pairs, tw, scale, st);
-        if (ro == 5) return launch_middle_odd<T, 5>(lg, mode, W, spec, L, pairs, tw, scale, st);
-        if (ro == 9) return launch_middle_odd<T, 9>(lg, mode, W, spec, L, pairs, tw, scale, st);
+        if (ro == 3) return launch_middle_odd<T, 3>(lg, mode, W, spec, L, pairs, tw, scale, st, err);
+        if (ro == 5) return launch_middle_odd<T, 5>(lg, mode, W, spec, L, pairs, tw, scale, st, err);
+        if (ro == 9) return launch_middle_odd<T, 9>(lg, mode, W, spec, L, pairs, tw, scale, st, err);
         return cudaErrorInvalidValue;
     }
 }
@@ -140,25 +194,25 @@ cudaError_t launch_middle(int ro, int lg, int mode, cx<T> *W, cx<T> *spec, uint6
 // Odd innermost lengths RO * 2^lg, lg in [kMinLgOdd, kMaxLgOdd], where the CTA fits.
 template <typename T, int RO, int LG = kMinLgOdd>
 cudaError_t odd_middle_dispatch(int lg, int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pairs, TwTab<T> tw,
-                                cx<T> scale, cudaStream_t st) {
+                                cx<T> scale, cudaStream_t st, uint32_t *err) {
     if constexpr (LG > kMaxLgOdd) {
         return cudaErrorInvalidValue;
     } else {
         if (lg == LG) {
             if constexpr (odd_inner_ok<T>(RO, LG, false)) {
-                return middle_at<T, RO * (1 << LG)>(mode, W, spec, L, pairs, tw, scale, st);
+                return middle_at<T, RO * (1 << LG)>(mode, W, spec, L, pairs, tw, scale, st, err);
             } else {
                 return cudaErrorInvalidValue;
             }
         }
-        return odd_middle_dispatch<T, RO, LG + 1>(lg, mode, W, spec, L, pairs, tw, scale, st);
+        return odd_middle_dispatch<T, RO, LG + 1>(lg, mode, W, spec, L, pairs, tw, scale, st, err);
     }
 }
 
 template <typename T, int RO>
 cudaError_t launch_middle_odd(int lg, int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pairs, TwTab<T> tw,
-                              cx<T> scale, cudaStream_t st) {
-    return odd_middle_dispatch<T, RO>(lg, mode, W, spec, L, pairs, tw, scale, st);
+                              cx<T> scale, cudaStream_t st, uint32_t *err) {
+    return odd_middle_dispatch<T, RO>(lg, mode, W, spec, L, pairs, tw, scale, st, err);
 }
 
 template <typename T>
@@ -186,7 +240,7 @@ cudaError_t launch_inv_bits(int lgLEN, const cx<T> *W, uint64_t L, uint64_t m, u
     template cudaError_t launch_mid<T>(int, bool, cx<T> *, uint64_t, uint32_t, uint32_t, TwTab<T>,               \
                                        cudaStream_t);                                                           \
     template cudaError_t launch_middle<T>(int, int, int, cx<T> *, cx<T> *, uint64_t, uint32_t, TwTab<T>, cx<T>,  \
-                                          cudaStream_t);                                                        \
+                                          cudaStream_t, uint32_t *);                                            \
     template cudaError_t launch_inv_bits<T>(int, const cx<T> *, uint64_t, uint64_t, uint32_t, const uint32_t *,  \
                                             uint32_t *, uint64_t *, uint64_t, uint32_t, TwTab<T>, cudaStream_t);
 
@@ -284,7 +338,7 @@ cudaError_t launch_inv_bits_blocks(int lgLEN, const cx<T> *Wi, uint64_t L, const
 // Odd innermost lengths of one (type, RO): the plain middle pass and the split pass.
 #define PA_INSTANTIATE_ODD(T, RO)                                                                               \
     template cudaError_t launch_middle_odd<T, RO>(int, int, cx<T> *, cx<T> *, uint64_t, uint32_t, TwTab<T>,     \
-                                                  cx<T>, cudaStream_t);                                         \
+                                                  cx<T>, cudaStream_t, uint32_t *);                             \
     template cudaError_t launch_middle_split_odd<T, RO>(int, const cx<T> *, cx<T> *, uint64_t, uint32_t,        \
                                                         uint32_t, uint32_t, TwTab<T>, cudaStream_t);
 

@@ -44,13 +44,16 @@ cudaError_t launch_fwd_seed(int lgLEN, const uint64_t *seed, uint64_t n, uint64_
 template <typename T>
 cudaError_t launch_mid(int lgLEN, bool inverse, cx<T> *W, uint64_t L, uint32_t S, uint32_t pairs, TwTab<T> tw,
                        cudaStream_t st);
-// Innermost pass of length ro * 2^lg.
+// Innermost pass of length ro * 2^lg. mode 0: the fused convolution step; mode 1:
+// the seed spectrum. With err != nullptr, mode 0 runs the persistent pipelined
+// kernel where its shared memory fits, and a copy wait that runs out of time sets
+// bit 0 of *err (device memory).
 template <typename T>
 cudaError_t launch_middle(int ro, int lg, int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pairs, TwTab<T> tw,
-                          cx<T> scale, cudaStream_t st);
+                          cx<T> scale, cudaStream_t st, uint32_t *err = nullptr);
 template <typename T, int RO>
 cudaError_t launch_middle_odd(int lg, int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pairs, TwTab<T> tw,
-                              cx<T> scale, cudaStream_t st);
+                              cx<T> scale, cudaStream_t st, uint32_t *err);
 
 // Limits of the odd innermost lengths RO * 2^lg: a CTA has RO * 2^lg / E threads
 // (at most 1024, or 512 per row for the two-row split kernel).

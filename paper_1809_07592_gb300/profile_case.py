@@ -1,9 +1,11 @@
 """One hash batch for profilers: ``python -m paper_1809_07592_gb300.profile_case``.
 
-Sets up one plan (seed spectrum computed) and hashes one batch of keys, so an
-external profiler run (``ncu -k regex:... -c N``) sees exactly one launch of each
-pass kernel after the seed transform. Inputs are the seeded synthetic keys of
-``inputs.py``; the CUDA path runs through the C ABI as in any other call.
+Sets up one plan (split autotuning, seed spectrum, one warm-up batch), then hashes
+one batch of keys between cudaProfilerStart and cudaProfilerStop, so a profiler
+run with ``--profile-from-start off`` sees exactly one launch of each pass kernel.
+``--split L1,L2,L3`` fixes the pass split instead of autotuning it. Inputs are
+the seeded synthetic keys of ``inputs.py``; the CUDA path runs through the C ABI
+as in any other call.
 """
 from __future__ import annotations
 
@@ -20,6 +22,7 @@ def main(argv=None) -> int:
     ap.add_argument("--m", type=int, default=1 << 18)
     ap.add_argument("--keys", type=int, default=32)
     ap.add_argument("--dtype", default="fp32_guard", choices=["fp32_guard", "fp64", "ntt64"])
+    ap.add_argument("--split", default=None, help="L1,L2,L3 (one of pa_plan_splits); default: autotuned")
     a = ap.parse_args(argv)
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import torch
@@ -35,10 +38,16 @@ def main(argv=None) -> int:
     kb[:, : keys.shape[1]] = keys
     sw = np.zeros(seed.size + (seed.size & 1), np.uint64)
     sw[: seed.size] = seed
-    plan = pa.Plan(a.n, a.m, a.dtype)
+    split = tuple(int(x) for x in a.split.split(",")) if a.split else None
+    plan = pa.Plan(a.n, a.m, a.dtype, split=split)
     plan.set_seed(torch.from_numpy(sw.view(np.int64)).cuda())
-    plan.hash(torch.from_numpy(kb.view(np.int64)).cuda())
+    dk = torch.from_numpy(kb.view(np.int64)).cuda()
+    plan.hash(dk)  # warm-up
     torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    plan.hash(dk)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     print("ok", plan.shape())
     plan.close()
     return 0

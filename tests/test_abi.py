@@ -40,3 +40,28 @@ def test_no_library_fft_or_blas_linked():
     import subprocess
     deps = subprocess.run(["ldd", path], capture_output=True, text=True).stdout
     assert "cufft" not in deps and "cublas" not in deps
+
+
+def test_split_listing_without_gpu():
+    """pa_plan_splits is host-only: every listed split multiplies out to one length L >= n+m-1."""
+    import paper_1809_07592_gb300 as pa
+    build.build()
+    for n, m, dtype in [(1 << 20, 1 << 18, pa.PA_FP32_GUARD), (1_000_000, 100_000, pa.PA_FP32_GUARD),
+                        (1_000_000, 500_000, pa.PA_FP64), (1 << 20, 1 << 19, pa.PA_NTT64),
+                        ((1 << 27), 1 << 24, pa.PA_FP32_GUARD), (5000, 1500, pa.PA_FP64)]:
+        splits = pa.pa_plan_splits(n, m, dtype)
+        assert splits, (n, m, dtype)
+        lengths = {a * b * c for a, b, c in splits}
+        assert len(lengths) == 1, splits
+        L = lengths.pop()
+        assert L >= n + m - 1 and L >= 4096
+        assert len(set(splits)) == len(splits)
+        if dtype == pa.PA_NTT64:
+            assert L & (L - 1) == 0
+    # the DV-QKD length 5 * 2^18 has a split for every level-1 pass 2^7 .. 2^10
+    assert sorted(a for a, _, _ in pa.pa_plan_splits(1 << 20, 1 << 18, pa.PA_FP32_GUARD)) == [128, 256, 512, 1024]
+    try:
+        pa.pa_plan_splits(10, 11, pa.PA_FP64)
+        raise AssertionError("m > n accepted")
+    except pa.PAError as e:
+        assert e.code == pa.PA_EINVAL

@@ -259,3 +259,94 @@ def test_smooth_three_level(dtype):
     rows = sample_rows(m, 150, seed=3)
     exp = oracle.toeplitz_rows(n, m, seed, key, rows)
     np.testing.assert_array_equal(unpack_rows(got, m)[0][rows.astype(np.int64)], exp)
+
+
+@pytest.mark.parametrize("dtype", MODES, ids=MODE_ID.get)
+@pytest.mark.parametrize("n,m", [(1 << 20, 1 << 18), (1_000_000, 100_000), (1_000_000, 500_000), (5000, 1500)])
+def test_every_split_bit_exact(n, m, dtype):
+    """Every pass split the autotuner can pick gives the same bits; sampled rows match the oracle."""
+    seed = inputs.bernoulli_bits(11, 1, n + m - 1)
+    keys = inputs.batch_keys(n, 3, base_seed=11)
+    splits = pa.pa_plan_splits(n, m, dtype)
+    rows = sample_rows(m, 120, seed=m)
+    exp = [oracle.toeplitz_rows(n, m, seed, keys[k], rows) for k in range(3)]
+    first = None
+    for split in splits:
+        plan = pa.Plan(n, m, dtype, split=split)
+        assert tuple(plan.shape()[1:]) == tuple(split)
+        plan.set_seed(to_dev(seed)[0])
+        out, (marg, mode, esc) = plan.hash(to_dev(keys), info=True)
+        torch.cuda.synchronize()
+        got = to_host(out, (m + 63) // 64)
+        plan.close()
+        assert esc == 0 and max(marg) < 0.1, (split, marg)
+        bits = unpack_rows(got, m)
+        for k in range(3):
+            np.testing.assert_array_equal(bits[k][rows.astype(np.int64)], exp[k], err_msg=f"split {split} key {k}")
+        if first is None:
+            first = got
+        else:
+            np.testing.assert_array_equal(got, first, err_msg=f"split {split}")
+    tuned = pa.Plan(n, m, dtype)
+    assert tuple(tuned.shape()[1:]) in {tuple(s) for s in splits}
+    tuned.close()
+
+
+def test_forced_split_rejects_unlisted():
+    with pytest.raises(pa.PAError) as e:
+        pa.Plan(1 << 20, 1 << 18, pa.PA_FP32_GUARD, split=(64, 64, 1))
+    assert e.value.code == pa.PA_EINVAL
+
+
+def test_async_issue_then_finish_matches_sync():
+    """Batches of three plans issued back to back, then finished: same bits as pa_hash_batch."""
+    cases = [(40000, 9000), (100003, 40001), (1 << 20, 1 << 18)]
+    plans, bufs = [], []
+    for i, (n, m) in enumerate(cases):
+        seed = inputs.bernoulli_bits(21 + i, 1, n + m - 1)
+        keys = inputs.batch_keys(n, 5, base_seed=21 + i)
+        p = pa.Plan(n, m, pa.PA_FP32_GUARD)
+        p.set_seed(to_dev(seed)[0])
+        dk = to_dev(keys)
+        ref = to_host(p.hash(dk), (m + 63) // 64)
+        ow = (m + 63) // 64 + ((m + 63) // 64 & 1)
+        out = torch.full((5, ow), -1, dtype=torch.int64, device="cuda")
+        plans.append(p)
+        bufs.append((dk, out, ref, n, m, seed, keys))
+    for p, (dk, out, *_rest) in zip(plans, bufs):
+        pa.pa_hash_batch_async(p.handle, dk, 5, dk.shape[1], out, out.shape[1])
+    with pytest.raises(pa.PAError) as e:  # one batch in flight per plan
+        pa.pa_hash_batch_async(plans[0].handle, bufs[0][0], 5, bufs[0][0].shape[1], bufs[0][1], bufs[0][1].shape[1])
+    assert e.value.code == pa.PA_EAGAIN
+    for p, (dk, out, ref, n, m, seed, keys) in zip(plans, bufs):
+        marg, mode, esc = pa.pa_batch_finish(p.handle, 5, info=True)
+        assert esc == 0 and max(marg) < 0.05
+        got = to_host(out, (m + 63) // 64)
+        np.testing.assert_array_equal(got, ref)
+        rows = sample_rows(m, 50, seed=1)
+        np.testing.assert_array_equal(unpack_rows(got, m)[4][rows.astype(np.int64)],
+                                      oracle.toeplitz_rows(n, m, seed, keys[4], rows))
+    with pytest.raises(pa.PAError) as e:  # nothing issued
+        pa.pa_batch_finish(plans[0].handle)
+    assert e.value.code == pa.PA_EINVAL
+    for p in plans:
+        p.close()
+
+
+def test_async_forced_escalation():
+    """The guard step of an issued batch escalates like pa_hash_batch (threshold -1: every key)."""
+    n, m = 65536, 6554
+    seed = inputs.bernoulli_bits(4, 1, n + m - 1)
+    keys = inputs.batch_keys(n, 3, base_seed=4)
+    p = pa.Plan(n, m, pa.PA_FP32_GUARD)
+    pa.pa_plan_set_guard(p.handle, -1.0)
+    p.set_seed(to_dev(seed)[0])
+    dk = to_dev(keys)
+    out = torch.empty((3, 104), dtype=torch.int64, device="cuda")
+    pa.pa_hash_batch_async(p.handle, dk, 3, dk.shape[1], out, out.shape[1])
+    marg, mode, esc = pa.pa_batch_finish(p.handle, 3, info=True)
+    assert esc == 3 and all(md in (pa.PA_FP64, pa.PA_NTT64) for md in mode)
+    got = to_host(out, (m + 63) // 64)
+    for k in range(3):
+        np.testing.assert_array_equal(got[k], oracle.toeplitz_hash(n, m, seed, keys[k]))
+    p.close()
