@@ -344,7 +344,7 @@ int run_keys(pa_plan_t *p, const uint64_t *keys, uint32_t nkeys, uint64_t kstrid
     cx<T> *W = static_cast<cx<T> *>(p->work);
     cx<T> *spec = static_cast<cx<T> *>(p->spec);
     const Geometry &g = p->geo;
-    { Timed t_(p, K_PREP, st); PA_CUDA(launch_prep(keys, nkeys, kstride, p->n, popc, marg, st)); }
+    { Timed t_(p, K_PREP, st); PA_CUDA(launch_zero_keys(nkeys, popc, marg, st)); }
     const uint32_t npairs = (nkeys + 1) / 2;
     for (uint32_t p0 = 0; p0 < npairs; p0 += p->work_pairs) {
         const uint32_t pairs = (npairs - p0 < p->work_pairs) ? npairs - p0 : p->work_pairs;
@@ -352,7 +352,7 @@ int run_keys(pa_plan_t *p, const uint64_t *keys, uint32_t nkeys, uint64_t kstrid
         const uint32_t nk = (nkeys - k0 < 2 * pairs) ? nkeys - k0 : 2 * pairs;
         const uint64_t *kp = keys + (uint64_t)k0 * kstride;
         uint64_t *op = out + (uint64_t)k0 * ostride;
-        { Timed t_(p, K_FWD_KEYS, st); PA_CUDA(launch_fwd_keys<T>(g.lg1, kp, nk, kstride, p->n, W, p->L, pairs, tw, st)); }
+        { Timed t_(p, K_FWD_KEYS, st); PA_CUDA(launch_fwd_keys<T>(g.lg1, kp, nk, kstride, p->n, W, p->L, pairs, tw, popc + k0, st)); }
         if (g.lgM) {
             { Timed t_(p, K_MID_FWD, st); PA_CUDA(launch_mid<T>(g.lgM, false, W, p->L, g.inner(), pairs, tw, st)); }
             { Timed t_(p, K_MIDDLE_CONV, st); PA_CUDA(launch_middle<T>(g.ro, g.lgI, 0, W, spec, p->L, pairs, tw, one<T>(), st, p->err)); }

@@ -91,11 +91,6 @@ template <> struct Enc<Zp> {
 };
 
 // ---------------------------------------------------------------------------
-// popcount P of each key (bits < n) and reset of its rounding margin.
-__global__ void k_prep(const uint64_t *__restrict__ keys, uint32_t nkeys, uint64_t kstride, uint64_t n,
-                       uint32_t *__restrict__ popc, uint32_t *__restrict__ margin_bits);
-
-// ---------------------------------------------------------------------------
 // Bit staging for the level-1 forward passes: per row, the CTA's COLS input bits
 // (low 16 bits: key or key a; high 16 bits: key b or seed) after the transform's
 // shared memory.
@@ -136,7 +131,7 @@ __device__ __forceinline__ uint32_t bits_at(const uint64_t *v, uint64_t nbits, u
 template <typename T, int LEN, int COLS, int E>
 __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
     k_fwd_keys(const uint64_t *__restrict__ keys, uint32_t nkeys, uint64_t kstride, uint64_t n,
-               cx<T> *__restrict__ W, uint64_t L, TwTab<T> tw) {
+               cx<T> *__restrict__ W, uint64_t L, TwTab<T> tw, uint32_t *__restrict__ popc) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T> *sm = reinterpret_cast<cx<T> *>(smem_raw);
     const uint32_t col = threadIdx.x % COLS, tq = threadIdx.x / COLS;
@@ -148,11 +143,20 @@ __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
     // one word load per row instead of one per element, all in flight together.
     uint32_t *stage = key_stage<T, LEN, COLS>(smem_raw);
     const uint64_t u0 = (uint64_t)blockIdx.x * COLS;
+    uint32_t ca = 0, cb = 0;  // the CTA's share of each key's popcount P (the CTAs tile every bit once)
     for (uint32_t a = threadIdx.x; a < LEN; a += blockDim.x) {
         const uint64_t t0 = (uint64_t)a * S + u0;  // S % 64 == 0: the COLS bits sit in one word
         const uint32_t wa = aligned_bits<COLS>(keys + (uint64_t)(2 * pair) * kstride, n, t0);
         const uint32_t wb = has_b ? aligned_bits<COLS>(keys + (uint64_t)(2 * pair + 1) * kstride, n, t0) : 0u;
         stage[a] = wa | (wb << 16);
+        ca += __popc(wa);
+        cb += __popc(wb);
+    }
+    ca = __reduce_add_sync(0xffffffffu, ca);
+    cb = __reduce_add_sync(0xffffffffu, cb);
+    if ((threadIdx.x & 31) == 0 && (ca | cb)) {
+        if (ca) atomicAdd(popc + 2 * pair, ca);
+        if (cb) atomicAdd(popc + 2 * pair + 1, cb);
     }
     __syncthreads();
     cx<T> v[E];
@@ -414,18 +418,18 @@ __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
     for (int s = 0; s < E; ++s) {
         const uint64_t t1 = idx_r0<LEN, E>(tq, s);
         const uint64_t i = t1 * S + u;
+        const uint64_t ci = (t1 * S + u0) / COLS;  // output chunk of this row's COLS bits
+        // rows past the last output word are not decoded (warp-uniform test: the ballot needs every lane)
+        if (!__any_sync(0xffffffffu, ci < nchunks)) continue;
         bool bit_a, bit_b;
         Enc<T>::decode(v[s], popa, popb, i < m, bit_a, bit_b, ma, mb);
         const uint32_t ba = __ballot_sync(0xffffffffu, bit_a);
         const uint32_t bb = __ballot_sync(0xffffffffu, bit_b);
-        if (col == 0) {
-            const uint64_t ci = (t1 * S + u0) / COLS;
+        if (col == 0 && ci < nchunks) {
             const uint32_t sh = lane;  // lane = group * COLS
             const uint32_t msk = (COLS == 32) ? 0xffffffffu : ((1u << COLS) - 1u);
-            if (ci < nchunks) {
-                oa[ci] = (word_t)((ba >> sh) & msk);
-                if (has_b) ob[ci] = (word_t)((bb >> sh) & msk);
-            }
+            oa[ci] = (word_t)((ba >> sh) & msk);
+            if (has_b) ob[ci] = (word_t)((bb >> sh) & msk);
         }
     }
     uint32_t fa = __float_as_uint(margin_to_float(ma)), fb = __float_as_uint(margin_to_float(mb));

@@ -44,7 +44,7 @@ static cudaError_t by_len(int lg, F &&f) {
 
 template <typename T>
 cudaError_t launch_fwd_keys(int lgLEN, const uint64_t *keys, uint32_t nkeys, uint64_t kstride, uint64_t n,
-                            cx<T> *W, uint64_t L, uint32_t pairs, TwTab<T> tw, cudaStream_t st) {
+                            cx<T> *W, uint64_t L, uint32_t pairs, TwTab<T> tw, uint32_t *popc, cudaStream_t st) {
     constexpr int E = Shape<T>::E, COLS = Shape<T>::COLS;
     return by_len<kMinLgStrided, kMaxLgStrided>(lgLEN, [&](auto c) {
         constexpr int LEN = decltype(c)::value;
@@ -53,7 +53,7 @@ cudaError_t launch_fwd_keys(int lgLEN, const uint64_t *keys, uint32_t nkeys, uin
         cudaError_t e = set_smem(kern, sb);
         if (e != cudaSuccess) return e;
         dim3 grid((unsigned)((L / LEN) / COLS), pairs);
-        kern<<<grid, COLS * LEN / E, sb, st>>>(keys, nkeys, kstride, n, W, L, tw);
+        kern<<<grid, COLS * LEN / E, sb, st>>>(keys, nkeys, kstride, n, W, L, tw, popc);
         return cudaGetLastError();
     });
 }
@@ -234,7 +234,7 @@ cudaError_t launch_inv_bits(int lgLEN, const cx<T> *W, uint64_t L, uint64_t m, u
 
 #define PA_INSTANTIATE_LAUNCHERS(T)                                                                              \
     template cudaError_t launch_fwd_keys<T>(int, const uint64_t *, uint32_t, uint64_t, uint64_t, cx<T> *,        \
-                                            uint64_t, uint32_t, TwTab<T>, cudaStream_t);                         \
+                                            uint64_t, uint32_t, TwTab<T>, uint32_t *, cudaStream_t);             \
     template cudaError_t launch_fwd_seed<T>(int, const uint64_t *, uint64_t, uint64_t, cx<T> *, uint64_t,        \
                                             TwTab<T>, cudaStream_t);                                             \
     template cudaError_t launch_mid<T>(int, bool, cx<T> *, uint64_t, uint32_t, uint32_t, TwTab<T>,               \

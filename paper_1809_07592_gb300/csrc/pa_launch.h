@@ -31,12 +31,14 @@ template <> struct MaxLgMiddle<double> { static constexpr int v = 13; };
 template <> struct MaxLgMiddle<Zp> { static constexpr int v = 13; };
 constexpr int kMinLgMiddle = 6;
 
-cudaError_t launch_prep(const uint64_t *keys, uint32_t nkeys, uint64_t kstride, uint64_t n, uint32_t *popc,
-                        uint32_t *margin_bits, cudaStream_t st);
+// Zero the per-key popcounts and margins of a batch (the level-1 forward pass accumulates the popcounts).
+cudaError_t launch_zero_keys(uint32_t nkeys, uint32_t *popc, uint32_t *margin_bits, cudaStream_t st);
 
+// Level-1 forward pass of key pairs; also adds each key's popcount into popc[k]
+// (which must be zero beforehand: launch_zero_keys).
 template <typename T>
 cudaError_t launch_fwd_keys(int lgLEN, const uint64_t *keys, uint32_t nkeys, uint64_t kstride, uint64_t n,
-                            cx<T> *W, uint64_t L, uint32_t pairs, TwTab<T> tw, cudaStream_t st);
+                            cx<T> *W, uint64_t L, uint32_t pairs, TwTab<T> tw, uint32_t *popc, cudaStream_t st);
 template <typename T>
 cudaError_t launch_fwd_seed(int lgLEN, const uint64_t *seed, uint64_t n, uint64_t m, cx<T> *W, uint64_t L,
                             TwTab<T> tw, cudaStream_t st);

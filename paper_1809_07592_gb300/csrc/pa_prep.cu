@@ -23,38 +23,23 @@ void smem_mark_configured(const void *kernel, int device) {
     g_smem_done.insert({kernel, device});
 }
 
-// One CTA per key. P = popcount of the key's bits below n; it enters the
-// rounding step as P mod 4 (see the encoding note in pa_kernels.cuh).
-__global__ void __launch_bounds__(256)
-    k_prep(const uint64_t *__restrict__ keys, uint32_t nkeys, uint64_t kstride, uint64_t n,
-           uint32_t *__restrict__ popc, uint32_t *__restrict__ margin_bits) {
-    const uint32_t key = blockIdx.x;
-    const uint64_t *k = keys + (uint64_t)key * kstride;
-    const uint64_t nw = (n + 63) >> 6;
-    uint32_t acc = 0;
-    for (uint64_t w = threadIdx.x; w < nw; w += blockDim.x) {
-        uint64_t x = __ldg(k + w);
-        if (w == nw - 1 && (n & 63)) x &= (1ull << (n & 63)) - 1ull;
-        acc += (uint32_t)__popcll(x);
-    }
-    acc = __reduce_add_sync(0xffffffffu, acc);
-    __shared__ uint32_t part[8];
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t t = 0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += part[i];
-        popc[key] = t;
-        margin_bits[key] = 0u;
+// Per-key state of a batch: the popcount P (accumulated by the level-1 forward
+// pass, which reads every key bit; it enters the rounding step as P mod 4, see the
+// encoding note in pa_kernels.cuh) and the rounding margin start at zero.
+__global__ void k_zero_keys(uint32_t nkeys, uint32_t *__restrict__ popc, uint32_t *__restrict__ margin_bits) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nkeys) {
+        popc[k] = 0u;
+        margin_bits[k] = 0u;
     }
 }
 
-cudaError_t launch_prep(const uint64_t *keys, uint32_t nkeys, uint64_t kstride, uint64_t n, uint32_t *popc,
-                        uint32_t *margin_bits, cudaStream_t st) {
+cudaError_t launch_zero_keys(uint32_t nkeys, uint32_t *popc, uint32_t *margin_bits, cudaStream_t st) {
     if (nkeys == 0) return cudaSuccess;
-    k_prep<<<nkeys, 256, 0, st>>>(keys, nkeys, kstride, n, popc, margin_bits);
+    k_zero_keys<<<(nkeys + 255) / 256, 256, 0, st>>>(nkeys, popc, margin_bits);
     return cudaGetLastError();
 }
+
 
 // One CTA per block of an uneven batch: popcount of its key (bits < n) into
 // popc[id], margin[id] reset.

@@ -165,8 +165,8 @@ int run_static(unsigned char *base, int lgL, uint64_t n, uint64_t m, const uint6
     tw.F = 1u << lgF;
     STATIC_CUDA(launch_fwd_seed<T>(lg1, seed, n, m, W, L, tw, st));
     STATIC_CUDA(launch_middle<T>(1, lg2, 1, W, spec, L, 1, tw, scale_of<T>(L), st));
-    STATIC_CUDA(launch_prep(keys, nkeys, kstride, n, popc, marg, st));  // also zeroes the margins
-    STATIC_CUDA(launch_fwd_keys<T>(lg1, keys, nkeys, kstride, n, W, L, 1, tw, st));
+    STATIC_CUDA(launch_zero_keys(nkeys, popc, marg, st));  // the forward pass accumulates the popcounts
+    STATIC_CUDA(launch_fwd_keys<T>(lg1, keys, nkeys, kstride, n, W, L, 1, tw, popc, st));
     STATIC_CUDA(launch_middle<T>(1, lg2, 0, W, spec, L, 1, tw, unit<T>(), st));
     STATIC_CUDA(launch_inv_bits<T>(lg1, W, L, m, nkeys, popc, marg, out, ostride, 1, tw, st));
     return PA_OK;

@@ -165,8 +165,8 @@ int run_class_ntt(const ClassRun &c, const pa_block_desc_t *hb, const uint32_t *
         U_CUDA(launch_fwd_seed<Zp>(g.lg1, b.seed, b.n, b.m, W, L, tw, st));
         if (g.lgM) U_CUDA(launch_mid<Zp>(g.lgM, false, W, L, g.inner(), 1, tw, st));
         U_CUDA(launch_middle<Zp>(g.ro, g.lgI, 1, W, spec, L, 1, tw, invL, st));
-        U_CUDA(launch_prep(b.key, 1, kw, b.n, popc + ids[i], marg + ids[i], st));
-        U_CUDA(launch_fwd_keys<Zp>(g.lg1, b.key, 1, kw, b.n, W, L, 1, tw, st));
+        U_CUDA(launch_zero_keys(1, popc + ids[i], marg + ids[i], st));
+        U_CUDA(launch_fwd_keys<Zp>(g.lg1, b.key, 1, kw, b.n, W, L, 1, tw, popc + ids[i], st));
         if (g.lgM) U_CUDA(launch_mid<Zp>(g.lgM, false, W, L, g.inner(), 1, tw, st));
         U_CUDA(launch_middle<Zp>(g.ro, g.lgI, 0, W, spec, L, 1, tw, (cx<Zp>)1, st));
         if (g.lgM) U_CUDA(launch_mid<Zp>(g.lgM, true, W, L, g.inner(), 1, tw, st));
