@@ -162,6 +162,29 @@ int pa_hash_batch_async(pa_plan_t *plan, const uint64_t *keys_dev, uint32_t nkey
 int pa_batch_finish(pa_plan_t *plan, pa_batch_info_t *info);
 
 /*
+ * pa_hash_host_async / pa_hash_host -- key ingestion and final-key egress around the
+ * hash (the QKD pipeline hands raw keys over in host memory and takes final keys
+ * back, the paper's Fig. 1): keys are copied from host memory into plan-owned
+ * device rows on a copy stream, hashed on `stream`, and the final keys copied back
+ * to host memory on a second copy stream, so consecutive batches (of this and of
+ * other plans) overlap their copies with each other's compute. The copies overlap
+ * only from pinned host memory (cudaHostAlloc / cudaHostRegister); pageable memory
+ * works but serialises.
+ *   keys_host          host pointer; key k starts at keys_host + k*key_stride_words (>= ceil(n/64))
+ *   out_host           host pointer; final key k at out_host + k*out_stride_words (>= ceil(m/64));
+ *                      only the ceil(m/64) words of each row are written (tail bits zero)
+ * pa_hash_host_async returns after issuing; pa_batch_finish (above) waits for the
+ * read-back, runs the guard, and rewrites in host memory the rows of the keys it
+ * recomputed. The host rows are final once pa_batch_finish returns PA_OK; the
+ * caller keeps both host buffers alive and unmodified until then. pa_hash_host is
+ * the two calls in one. Errors as pa_hash_batch (no alignment rule for host pointers).
+ */
+int pa_hash_host_async(pa_plan_t *plan, const uint64_t *keys_host, uint32_t nkeys, uint64_t key_stride_words,
+                       uint64_t *out_host, uint64_t out_stride_words, pa_stream_t stream);
+int pa_hash_host(pa_plan_t *plan, const uint64_t *keys_host, uint32_t nkeys, uint64_t key_stride_words,
+                 uint64_t *out_host, uint64_t out_stride_words, pa_stream_t stream, pa_batch_info_t *info);
+
+/*
  * pa_plan_set_guard -- rounding-margin threshold of the FP32 guard (default 0.25,
  * the value the guard is specified with). A key whose margin max_i |w_i - rint(w_i)|
  * exceeds it is recomputed in FP64. Lowering it (e.g. to -1) forces every key

@@ -99,6 +99,8 @@ def lib():
     L.pa_plan_set_guard.argtypes = [vp, ctypes.c_float]
     L.pa_hash_batch_async.argtypes = [vp, vp, u32, u64, vp, u64, vp]
     L.pa_batch_finish.argtypes = [vp, ctypes.POINTER(BatchInfo)]
+    L.pa_hash_host_async.argtypes = [vp, vp, u32, u64, vp, u64, vp]
+    L.pa_hash_host.argtypes = [vp, vp, u32, u64, vp, u64, vp, ctypes.POINTER(BatchInfo)]
     L.pa_plan_shape.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u32), ctypes.POINTER(u32),
                                 ctypes.POINTER(u32)]
     L.pa_plan_splits.argtypes = [u64, u64, ctypes.c_int, ctypes.POINTER(u32), ctypes.POINTER(u32),
@@ -126,7 +128,7 @@ def lib():
     L.pa_last_cuda_error.argtypes = []
     L.pa_last_cuda_error.restype = ctypes.c_char_p
     for name in ("pa_plan", "pa_plan_destroy", "pa_set_seed", "pa_hash_batch", "pa_hash_batch_async",
-                 "pa_batch_finish", "pa_plan_set_guard",
+                 "pa_batch_finish", "pa_hash_host_async", "pa_hash_host", "pa_plan_set_guard",
                  "pa_plan_shape", "pa_plan_splits", "pa_plan_split", "pa_profile_enable", "pa_profile_read", "pa_uneven_create", "pa_uneven_update",
                  "pa_uneven_run", "pa_uneven_set_guard", "pa_uneven_destroy", "pa_uneven_class", "pa_hash_uneven",
                  "pa_server_create", "pa_submit", "pa_poll", "pa_wait", "pa_server_stats", "pa_server_destroy"):
@@ -229,6 +231,26 @@ def pa_hash_batch_async(plan: int, keys, nkeys: int, key_stride_words: int, out,
     """Issue a batch (kernels + margin read-back) without waiting; finish it with pa_batch_finish."""
     _check(lib().pa_hash_batch_async(plan, _ptr(keys), nkeys, key_stride_words, _ptr(out), out_stride_words,
                                      _stream_handle(stream)), "pa_hash_batch_async")
+
+
+def _host_ptr(t) -> int:
+    if t.is_cuda:
+        raise ValueError("expected a host (CPU) tensor")
+    return t.data_ptr()
+
+
+def pa_hash_host_async(plan: int, keys, nkeys: int, key_stride_words: int, out, out_stride_words: int,
+                       stream=None) -> None:
+    """Host keys in, host final keys out (pinned CPU tensors overlap); finish with pa_batch_finish."""
+    _check(lib().pa_hash_host_async(plan, _host_ptr(keys), nkeys, key_stride_words, _host_ptr(out), out_stride_words,
+                                    _stream_handle(stream)), "pa_hash_host_async")
+
+
+def pa_hash_host(plan: int, keys, nkeys: int, key_stride_words: int, out, out_stride_words: int, stream=None,
+                 info: bool = False):
+    """pa_hash_host_async + pa_batch_finish; (margins, modes, escalated) when ``info`` is set."""
+    pa_hash_host_async(plan, keys, nkeys, key_stride_words, out, out_stride_words, stream)
+    return pa_batch_finish(plan, nkeys, info)
 
 
 def pa_batch_finish(plan: int, nkeys: int = 0, info: bool = False):

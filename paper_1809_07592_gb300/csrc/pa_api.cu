@@ -60,12 +60,14 @@ inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 
 // The arguments of an issued batch, kept for its guard step.
 struct PendingBatch {
     bool active = false;
-    const uint64_t *keys = nullptr;
+    const uint64_t *keys = nullptr;  // device rows the kernels read
     uint32_t nkeys = 0;
     uint64_t kstride = 0;
-    uint64_t *out = nullptr;
+    uint64_t *out = nullptr;  // device rows the kernels write
     uint64_t ostride = 0;
     pa_stream_t stream = nullptr;
+    uint64_t *host_out = nullptr;  // host batches: where the final keys go
+    uint64_t host_ostride = 0;
 };
 
 struct pa_plan {
@@ -92,7 +94,12 @@ struct pa_plan {
     float guard = 0.25f;
     pa_plan_t *fallback = nullptr;    // next-wider plan (FP32 -> FP64 -> NTT64) for keys that fail the guard
     PendingBatch pending;             // a batch issued by pa_hash_batch_async, not yet finished
-    cudaEvent_t done = nullptr;       // recorded behind the margins' read-back
+    cudaEvent_t done = nullptr;       // recorded behind the margins' (and host outputs') read-back
+    // host batches (pa_hash_host_async): device staging rows and the copy streams around the compute
+    uint64_t *stage_keys = nullptr, *stage_out = nullptr;
+    size_t stage_key_words = 0, stage_out_words = 0;
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_comp = nullptr;
     std::mutex mu;
     // kernel timing
     bool prof = false;
@@ -380,6 +387,12 @@ void free_plan(pa_plan_t *p) {
     cudaFree(p->seed_copy);
     if (p->h_marg) cudaFreeHost(p->h_marg);
     if (p->done) cudaEventDestroy(p->done);
+    cudaFree(p->stage_keys);
+    cudaFree(p->stage_out);
+    if (p->ev_in) cudaEventDestroy(p->ev_in);
+    if (p->ev_comp) cudaEventDestroy(p->ev_comp);
+    if (p->s_in) cudaStreamDestroy(p->s_in);
+    if (p->s_out) cudaStreamDestroy(p->s_out);
     for (cudaEvent_t e : p->ev_a) cudaEventDestroy(e);
     for (cudaEvent_t e : p->ev_b) cudaEventDestroy(e);
     delete p;
@@ -575,8 +588,71 @@ int escalate_key(pa_plan_t *p, const PendingBatch &b, uint32_t k, float *margin,
     int rc = pa_hash_batch(p->fallback, b.keys + (uint64_t)k * b.kstride, 1, b.kstride, b.out + (uint64_t)k * b.ostride,
                            b.ostride, b.stream, &sub);
     if (rc != PA_OK) return rc;
+    if (b.host_out) {  // the batch's read-back carried the first result: replace this key's row
+        cudaStream_t st = reinterpret_cast<cudaStream_t>(b.stream);
+        PA_CUDA(cudaMemcpyAsync(b.host_out + (uint64_t)k * b.host_ostride, b.out + (uint64_t)k * b.ostride,
+                                (size_t)((p->m + 63) / 64) * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+        PA_CUDA(cudaStreamSynchronize(st));
+    }
     *margin = m2;
     *mode = mode2;
+    return PA_OK;
+}
+
+// Kernels of one batch and the read-back of its margins and error word, on st.
+int issue_batch(pa_plan_t *p, const uint64_t *keys_dev, uint32_t nkeys, uint64_t kstride, uint64_t *out_dev,
+                uint64_t ostride, cudaStream_t st) {
+    const uint32_t npairs = (nkeys + 1) / 2;
+    uint32_t want = npairs < p->max_chunk_pairs ? npairs : p->max_chunk_pairs;
+    int rc = ensure_work(p, want);
+    if (rc != PA_OK) return rc;
+    rc = ensure_keys(p, nkeys);
+    if (rc != PA_OK) return rc;
+    rc = ensure_host(p, nkeys);
+    if (rc != PA_OK) return rc;
+    if (!p->done) PA_CUDA(cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming));
+    if (p->dtype == PA_FP32_GUARD)
+        rc = run_keys<float>(p, keys_dev, nkeys, kstride, out_dev, ostride, p->popc, p->marg, st);
+    else if (p->dtype == PA_FP64)
+        rc = run_keys<double>(p, keys_dev, nkeys, kstride, out_dev, ostride, p->popc, p->marg, st);
+    else
+        rc = run_keys<Zp>(p, keys_dev, nkeys, kstride, out_dev, ostride, p->popc, p->marg, st);
+    if (rc != PA_OK) return rc;
+    // the margins and the error word travel back behind the kernels; pa_batch_finish waits for them
+    PA_CUDA(cudaMemcpyAsync(p->h_marg, p->marg, (size_t)nkeys * sizeof(float), cudaMemcpyDeviceToHost, st));
+    PA_CUDA(cudaMemcpyAsync(p->h_marg + nkeys, p->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    return PA_OK;
+}
+
+int ensure_staging(pa_plan_t *p, size_t key_words, size_t out_words) {
+    if (key_words > p->stage_key_words) {
+        cudaFree(p->stage_keys);
+        p->stage_keys = nullptr;
+        p->stage_key_words = 0;
+        cudaError_t e = cudaMalloc(&p->stage_keys, key_words * sizeof(uint64_t));
+        if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();
+            return PA_ENOMEM;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(stage_keys)");
+        p->stage_key_words = key_words;
+    }
+    if (out_words > p->stage_out_words) {
+        cudaFree(p->stage_out);
+        p->stage_out = nullptr;
+        p->stage_out_words = 0;
+        cudaError_t e = cudaMalloc(&p->stage_out, out_words * sizeof(uint64_t));
+        if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();
+            return PA_ENOMEM;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(stage_out)");
+        p->stage_out_words = out_words;
+    }
+    if (!p->s_in) PA_CUDA(cudaStreamCreateWithFlags(&p->s_in, cudaStreamNonBlocking));
+    if (!p->s_out) PA_CUDA(cudaStreamCreateWithFlags(&p->s_out, cudaStreamNonBlocking));
+    if (!p->ev_in) PA_CUDA(cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming));
+    if (!p->ev_comp) PA_CUDA(cudaEventCreateWithFlags(&p->ev_comp, cudaEventDisableTiming));
     return PA_OK;
 }
 
@@ -728,28 +804,67 @@ int pa_hash_batch_async(pa_plan_t *p, const uint64_t *keys_dev, uint32_t nkeys, 
     DeviceGuard g(p->device);
     if (!g.ok) return cuda_fail(cudaGetLastError(), "cudaSetDevice");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const uint32_t npairs = (nkeys + 1) / 2;
-    uint32_t want = npairs < p->max_chunk_pairs ? npairs : p->max_chunk_pairs;
-    int rc = ensure_work(p, want);
+    int rc = issue_batch(p, keys_dev, nkeys, key_stride_words, out_dev, out_stride_words, st);
     if (rc != PA_OK) return rc;
-    rc = ensure_keys(p, nkeys);
-    if (rc != PA_OK) return rc;
-    rc = ensure_host(p, nkeys);
-    if (rc != PA_OK) return rc;
-    if (!p->done) PA_CUDA(cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming));
-    if (p->dtype == PA_FP32_GUARD)
-        rc = run_keys<float>(p, keys_dev, nkeys, key_stride_words, out_dev, out_stride_words, p->popc, p->marg, st);
-    else if (p->dtype == PA_FP64)
-        rc = run_keys<double>(p, keys_dev, nkeys, key_stride_words, out_dev, out_stride_words, p->popc, p->marg, st);
-    else
-        rc = run_keys<Zp>(p, keys_dev, nkeys, key_stride_words, out_dev, out_stride_words, p->popc, p->marg, st);
-    if (rc != PA_OK) return rc;
-    // the margins and the error word travel back behind the kernels; pa_batch_finish waits for them
-    PA_CUDA(cudaMemcpyAsync(p->h_marg, p->marg, (size_t)nkeys * sizeof(float), cudaMemcpyDeviceToHost, st));
-    PA_CUDA(cudaMemcpyAsync(p->h_marg + nkeys, p->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     PA_CUDA(cudaEventRecord(p->done, st));
-    p->pending = PendingBatch{true, keys_dev, nkeys, key_stride_words, out_dev, out_stride_words, stream};
+    PendingBatch b;
+    b.active = true;
+    b.keys = keys_dev;
+    b.nkeys = nkeys;
+    b.kstride = key_stride_words;
+    b.out = out_dev;
+    b.ostride = out_stride_words;
+    b.stream = stream;
+    p->pending = b;
     return PA_OK;
+}
+
+int pa_hash_host_async(pa_plan_t *p, const uint64_t *keys_host, uint32_t nkeys, uint64_t key_stride_words,
+                       uint64_t *out_host, uint64_t out_stride_words, pa_stream_t stream) {
+    if (!p || !keys_host || !out_host || nkeys == 0) return PA_EINVAL;
+    const uint64_t kw = (p->n + 63) / 64, ow = (p->m + 63) / 64;
+    if (key_stride_words < kw || out_stride_words < ow) return PA_EINVAL;
+    if (!p->seeded) return PA_ENOSEED;
+    std::lock_guard<std::mutex> lk(p->mu);
+    if (p->pending.active) return PA_EAGAIN;
+    DeviceGuard g(p->device);
+    if (!g.ok) return cuda_fail(cudaGetLastError(), "cudaSetDevice");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const uint64_t dks = kw + (kw & 1), dos = ow + (ow & 1);  // even device strides: 16-byte aligned rows
+    int rc = ensure_staging(p, (size_t)nkeys * dks, (size_t)nkeys * dos);
+    if (rc != PA_OK) return rc;
+    // keys in on their own stream, so they can overlap the compute of the batch before
+    PA_CUDA(cudaMemcpy2DAsync(p->stage_keys, dks * sizeof(uint64_t), keys_host, key_stride_words * sizeof(uint64_t),
+                              kw * sizeof(uint64_t), nkeys, cudaMemcpyHostToDevice, p->s_in));
+    PA_CUDA(cudaEventRecord(p->ev_in, p->s_in));
+    PA_CUDA(cudaStreamWaitEvent(st, p->ev_in, 0));
+    rc = issue_batch(p, p->stage_keys, nkeys, dks, p->stage_out, dos, st);
+    if (rc != PA_OK) return rc;
+    // final keys out on a third stream, so they overlap the compute of the batch after
+    PA_CUDA(cudaEventRecord(p->ev_comp, st));
+    PA_CUDA(cudaStreamWaitEvent(p->s_out, p->ev_comp, 0));
+    PA_CUDA(cudaMemcpy2DAsync(out_host, out_stride_words * sizeof(uint64_t), p->stage_out, dos * sizeof(uint64_t),
+                              ow * sizeof(uint64_t), nkeys, cudaMemcpyDeviceToHost, p->s_out));
+    PA_CUDA(cudaEventRecord(p->done, p->s_out));
+    PendingBatch b;
+    b.active = true;
+    b.keys = p->stage_keys;
+    b.nkeys = nkeys;
+    b.kstride = dks;
+    b.out = p->stage_out;
+    b.ostride = dos;
+    b.stream = stream;
+    b.host_out = out_host;
+    b.host_ostride = out_stride_words;
+    p->pending = b;
+    return PA_OK;
+}
+
+int pa_hash_host(pa_plan_t *p, const uint64_t *keys_host, uint32_t nkeys, uint64_t key_stride_words, uint64_t *out_host,
+                 uint64_t out_stride_words, pa_stream_t stream, pa_batch_info_t *info) {
+    int rc = pa_hash_host_async(p, keys_host, nkeys, key_stride_words, out_host, out_stride_words, stream);
+    if (rc != PA_OK) return rc;
+    return pa_batch_finish(p, info);
 }
 
 int pa_batch_finish(pa_plan_t *p, pa_batch_info_t *info) {

@@ -350,3 +350,83 @@ def test_async_forced_escalation():
     for k in range(3):
         np.testing.assert_array_equal(got[k], oracle.toeplitz_hash(n, m, seed, keys[k]))
     p.close()
+
+
+def _host_rows(arr_u64, stride, pinned):
+    """(nkeys, stride) int64 CPU tensor holding arr_u64 rows (padding words = a marker)."""
+    nk, nw = arr_u64.shape
+    t = torch.full((nk, stride), 0x5A5A, dtype=torch.int64)
+    if pinned:
+        t = t.pin_memory()
+    t[:, :nw] = torch.from_numpy(arr_u64.view(np.int64))
+    return t
+
+
+@pytest.mark.parametrize("pinned", [True, False], ids=["pinned", "pageable"])
+@pytest.mark.parametrize("dtype", MODES, ids=MODE_ID.get)
+def test_host_buffers_bit_exact(dtype, pinned):
+    """Keys from host memory, final keys back to host memory (odd strides, padding untouched)."""
+    n, m, nk = 100003, 40001, 5
+    seed = inputs.bernoulli_bits(31, 1, n + m - 1)
+    keys = inputs.batch_keys(n, nk, base_seed=31)
+    kw, ow = (n + 63) // 64, (m + 63) // 64
+    hk = _host_rows(keys, kw + 3, pinned)
+    ho = torch.full((nk, ow + 5), 0x77, dtype=torch.int64)
+    if pinned:
+        ho = ho.pin_memory()
+    p = pa.Plan(n, m, dtype)
+    p.set_seed(to_dev(seed)[0])
+    marg, mode, esc = pa.pa_hash_host(p.handle, hk, nk, hk.shape[1], ho, ho.shape[1], info=True)
+    p.close()
+    got = ho.numpy().view(np.uint64)
+    for k in range(nk):
+        np.testing.assert_array_equal(got[k, :ow], oracle.toeplitz_hash(n, m, seed, keys[k]), err_msg=f"key {k}")
+    assert (ho.numpy()[:, ow:] == 0x77).all()  # words past each row untouched
+    assert esc == 0 and max(marg) < 0.05
+
+
+def test_host_buffers_escalation_rewrites_rows():
+    """A key recomputed by the guard is rewritten in host memory."""
+    n, m, nk = 65536, 6554, 3
+    seed = inputs.bernoulli_bits(8, 1, n + m - 1)
+    keys = inputs.batch_keys(n, nk, base_seed=8)
+    hk = _host_rows(keys, (n + 63) // 64, True)
+    ow = (m + 63) // 64
+    ho = torch.zeros((nk, ow), dtype=torch.int64).pin_memory()
+    p = pa.Plan(n, m, pa.PA_FP32_GUARD)
+    pa.pa_plan_set_guard(p.handle, -1.0)
+    p.set_seed(to_dev(seed)[0])
+    marg, mode, esc = pa.pa_hash_host(p.handle, hk, nk, hk.shape[1], ho, ow, info=True)
+    p.close()
+    assert esc == nk
+    got = ho.numpy().view(np.uint64)
+    for k in range(nk):
+        np.testing.assert_array_equal(got[k], oracle.toeplitz_hash(n, m, seed, keys[k]))
+
+
+def test_host_buffers_three_plans_pipelined():
+    """Host batches of three plans issued back to back (copies overlap compute), then finished."""
+    cases = [(40000, 9000), (1 << 20, 1 << 18), (100003, 40001)]
+    plans, bufs = [], []
+    for i, (n, m) in enumerate(cases):
+        seed = inputs.bernoulli_bits(50 + i, 1, n + m - 1)
+        keys = inputs.batch_keys(n, 4, base_seed=50 + i)
+        p = pa.Plan(n, m, pa.PA_FP32_GUARD)
+        p.set_seed(to_dev(seed)[0])
+        hk = _host_rows(keys, (n + 63) // 64, True)
+        ho = torch.zeros((4, (m + 63) // 64), dtype=torch.int64).pin_memory()
+        plans.append(p)
+        bufs.append((hk, ho, n, m, seed, keys))
+    for _ in range(2):  # twice: the second round reuses the staging rows
+        for p, (hk, ho, *_r) in zip(plans, bufs):
+            ho.zero_()
+            pa.pa_hash_host_async(p.handle, hk, 4, hk.shape[1], ho, ho.shape[1])
+        for p, (hk, ho, n, m, seed, keys) in zip(plans, bufs):
+            pa.pa_batch_finish(p.handle)
+            got = ho.numpy().view(np.uint64)
+            rows = sample_rows(m, 60, seed=2)
+            for k in (0, 3):
+                np.testing.assert_array_equal(unpack_rows(got, m)[k][rows.astype(np.int64)],
+                                              oracle.toeplitz_rows(n, m, seed, keys[k], rows))
+    for p in plans:
+        p.close()
