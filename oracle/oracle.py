@@ -9,6 +9,12 @@ Toeplitz matrix T[i][j] = s[i - j + n - 1] built from an (n+m-1)-bit seed s,
 and the final key is y_i = XOR_j T[i][j] AND x_j. The C code evaluates that
 definition directly (bit-parallel AND + popcount parity, O(n m)).
 
+The modified Toeplitz hash of Section 2.2 (Eq. 2-3) is the identity block
+next to a Toeplitz block: y = x_[0,m) XOR T' x_[m,n), T' the m x (n-m)
+Toeplitz matrix of an (n-1)-bit seed. ``modified_hash`` evaluates Eq. 3's two
+terms as written: the first m key bits, XOR the Toeplitz product (above) of
+the remaining n-m key bits.
+
 Pins (``tests/test_oracle_pins.py``): dense brute force for n <= 64 and every
 key for tiny n, GF(2) linearity in key and seed, Toeplitz shift structure,
 special cases (unit key, all-ones seed, single-one seed, m = 1), hand-worked
@@ -109,3 +115,34 @@ def toeplitz_row_range(n: int, m: int, seed, key, row0: int, row1: int, threads:
     if rc != 0:
         raise ValueError(f"pa_oracle_hash_rows rc={rc}")
     return out
+
+
+def key_bits_from(key, nbits: int, start: int) -> np.ndarray:
+    """Bits [start, nbits) of a packed bit-vector, repacked from bit 0 (tail zero)."""
+    b = np.unpackbits(np.ascontiguousarray(key, dtype="<u8").view(np.uint8), bitorder="little")[start:nbits]
+    nw = (b.size + 63) // 64
+    pad = np.zeros(nw * 64, dtype=np.uint8)
+    pad[: b.size] = b
+    return np.packbits(pad, bitorder="little").view("<u8").astype(np.uint64)
+
+
+def modified_hash(n: int, m: int, seed, key, threads: int | None = None) -> np.ndarray:
+    """Eq. 3: y = X_r + V X_(n-r) with r = m, V the m x (n-m) Toeplitz block of the (n-1)-bit seed
+    (entry (i, j) = seed[i - j + n - m - 1], the orientation of toeplitz_hash). 1 <= m < n."""
+    if not 1 <= m < n:
+        raise ValueError("the modified Toeplitz hash needs 1 <= m < n")
+    key = _words(key, n)
+    tail = key_bits_from(key, n, m)                    # X_(n-r): key bits m .. n-1
+    y = toeplitz_hash(n - m, m, seed, tail, threads)   # V X_(n-r)
+    head = key_bits_from(key, m, 0)                    # X_r: key bits 0 .. m-1
+    return y ^ head
+
+
+def modified_rows(n: int, m: int, seed, key, rows, threads: int | None = None) -> np.ndarray:
+    """Selected output bits of modified_hash (uint8 array, one bit each)."""
+    key = _words(key, n)
+    tail = key_bits_from(key, n, m)
+    y = toeplitz_rows(n - m, m, seed, tail, rows, threads)
+    rows = np.asarray(rows, dtype=np.int64)
+    head = np.unpackbits(np.ascontiguousarray(key, dtype="<u8").view(np.uint8), bitorder="little")[rows]
+    return (y ^ head).astype(np.uint8)

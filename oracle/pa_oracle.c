@@ -24,6 +24,10 @@
  * i is the parity of popcount(s[i .. i+n-1] AND xr), evaluated 64 bits at a
  * time. Rows are independent and are split across POSIX threads.
  *
+ * The definition holds for any n, m >= 1 (a tall block, m > n, reads the same
+ * n+m-1 seed bits); the product's API limits the standard hash to m <= n, and
+ * the modified Toeplitz hash of Eq. 2-3 uses blocks with m > n.
+ *
  * Packed layout: bit j of a bit-vector is bit (j % 64) of 64-bit word j/64.
  * Key bits at positions >= n and seed bits at positions >= n+m-1 are
  * ignored; output bits at positions >= m are written as zero.
@@ -92,7 +96,7 @@ static void *worker(void *arg) {
  */
 int pa_oracle_hash_rows(uint64_t n, uint64_t m, const uint64_t *seed, const uint64_t *key,
                         uint64_t row0, uint64_t row1, uint64_t *out, int threads) {
-    if (n == 0 || m == 0 || m > n || !seed || !key || !out || row0 > row1 || row1 > m) return ORACLE_EINVAL;
+    if (n == 0 || m == 0 || !seed || !key || !out || row0 > row1 || row1 > m) return ORACLE_EINVAL;
     uint64_t nw = nwords(n);
     uint64_t *xr = (uint64_t *)calloc(nw ? nw : 1, sizeof(uint64_t));
     if (!xr) return ORACLE_ENOMEM;
@@ -144,7 +148,7 @@ int pa_oracle_hash(uint64_t n, uint64_t m, const uint64_t *seed, const uint64_t 
 
 /* One output bit, for spot checks at sizes where all rows would take too long. */
 int pa_oracle_row(uint64_t n, uint64_t m, const uint64_t *seed, const uint64_t *key, uint64_t i) {
-    if (n == 0 || m == 0 || m > n || i >= m || !seed || !key) return ORACLE_EINVAL;
+    if (n == 0 || m == 0 || i >= m || !seed || !key) return ORACLE_EINVAL;
     uint64_t nw = nwords(n);
     uint64_t *xr = (uint64_t *)calloc(nw, sizeof(uint64_t));
     if (!xr) return ORACLE_ENOMEM;
@@ -175,7 +179,7 @@ static void *rows_worker(void *arg) {
 
 int pa_oracle_rows(uint64_t n, uint64_t m, const uint64_t *seed, const uint64_t *key, const uint64_t *rows,
                    uint64_t nrows, uint8_t *bits, int threads) {
-    if (n == 0 || m == 0 || m > n || !seed || !key || (nrows && (!rows || !bits))) return ORACLE_EINVAL;
+    if (n == 0 || m == 0 || !seed || !key || (nrows && (!rows || !bits))) return ORACLE_EINVAL;
     for (uint64_t k = 0; k < nrows; ++k)
         if (rows[k] >= m) return ORACLE_EINVAL;
     uint64_t nw = nwords(n);

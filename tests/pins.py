@@ -88,3 +88,25 @@ def paper_orientation_hash(n: int, m: int, v_bits: np.ndarray, x_bits: np.ndarra
             acc ^= int(v_bits[m - 1 - i + j]) & int(x_bits[j])
         y[i] = acc
     return y
+
+
+def dense_modified(n: int, m: int, s: np.ndarray) -> np.ndarray:
+    """The modified Toeplitz matrix of Section 2.2 (Eq. 2): [I_m | T'] with T' the m x (n-m)
+    Toeplitz matrix of the (n-1)-bit seed s (built by dense_toeplitz from first row and column)."""
+    S = np.zeros((m, n), dtype=np.int64)
+    S[:, :m] = np.eye(m, dtype=np.int64)
+    S[:, m:] = dense_toeplitz(n - m, m, s)
+    return S
+
+
+def paper_modified_hash(n: int, m: int, v_bits: np.ndarray, x_bits: np.ndarray) -> np.ndarray:
+    """Eq. 2-3 in the layout the paper prints: identity on the first r = m columns, then the block
+    V with entry (i, j) = V_{r-1-i+j}, j < n-r (V has n-1 bits); y = X_r + V X_(n-r)."""
+    r = m
+    y = np.zeros(m, dtype=np.int64)
+    for i in range(m):
+        acc = int(x_bits[i])
+        for j in range(n - r):
+            acc ^= int(v_bits[r - 1 - i + j]) & int(x_bits[r + j])
+        y[i] = acc
+    return y

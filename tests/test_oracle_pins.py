@@ -233,3 +233,62 @@ def test_pins_catch_planted_mistakes(name, tmp_path):
             caught = True
             break
     assert caught, f"planted mistake {name} was not caught"
+
+
+# ---- modified Toeplitz matrix (Section 2.2, Eq. 2-3) ---------------------------------------------
+@pytest.mark.parametrize("n,m", [(2, 1), (5, 2), (17, 16), (33, 7), (64, 1), (64, 63), (65, 30), (130, 65)])
+def test_modified_brute_force(n, m):
+    """[I_m | T'] x mod 2 written out densely equals the oracle's Eq. 3 evaluation."""
+    rng = np.random.default_rng(n * 1000 + m)
+    s = rng.integers(0, 2, n - 1)
+    x = rng.integers(0, 2, n)
+    exp = (pins.dense_modified(n, m, s) @ x) % 2
+    got = pins.bits_of(oracle.modified_hash(n, m, pins.words_of(s), pins.words_of(x)), m)
+    np.testing.assert_array_equal(got, exp)
+
+
+@pytest.mark.parametrize("n,m", [(9, 4), (40, 13), (100, 99)])
+def test_modified_paper_orientation(n, m):
+    """The paper's printed layout (V_{r-1-i+j}) is the same hash with the seed reversed."""
+    rng = np.random.default_rng(7 * n + m)
+    s = rng.integers(0, 2, n - 1)
+    x = rng.integers(0, 2, n)
+    got = pins.bits_of(oracle.modified_hash(n, m, pins.words_of(s), pins.words_of(x)), m)
+    np.testing.assert_array_equal(got, pins.paper_modified_hash(n, m, s[::-1].copy(), x))
+
+
+def test_modified_special_cases():
+    n, m = 300, 70
+    rng = np.random.default_rng(3)
+    s = rng.integers(0, 2, n - 1)
+    x = rng.integers(0, 2, n)
+    head = x[:m]
+    # all-zero seed: the Toeplitz block vanishes, the final key is the first m key bits
+    got = pins.bits_of(oracle.modified_hash(n, m, pins.words_of(np.zeros(n - 1, np.int64)), pins.words_of(x)), m)
+    np.testing.assert_array_equal(got, head)
+    # key zero past bit m: same
+    x2 = x.copy()
+    x2[m:] = 0
+    got = pins.bits_of(oracle.modified_hash(n, m, pins.words_of(s), pins.words_of(x2)), m)
+    np.testing.assert_array_equal(got, head)
+    # key zero in its first m bits: the plain Toeplitz product of the remaining bits
+    x3 = x.copy()
+    x3[:m] = 0
+    got = pins.bits_of(oracle.modified_hash(n, m, pins.words_of(s), pins.words_of(x3)), m)
+    np.testing.assert_array_equal(got, pins.brute_hash(n - m, m, s, x3[m:]))
+    # rows helper
+    rows = np.array([0, 1, m // 2, m - 1], dtype=np.uint64)
+    full = pins.bits_of(oracle.modified_hash(n, m, pins.words_of(s), pins.words_of(x)), m)
+    np.testing.assert_array_equal(oracle.modified_rows(n, m, pins.words_of(s), pins.words_of(x), rows),
+                                  full[rows.astype(np.int64)])
+    with pytest.raises(ValueError):
+        oracle.modified_hash(n, n, pins.words_of(s), pins.words_of(x))
+
+
+def test_modified_linearity():
+    n, m = 200, 61
+    rng = np.random.default_rng(11)
+    s = pins.words_of(rng.integers(0, 2, n - 1))
+    a, b = pins.words_of(rng.integers(0, 2, n)), pins.words_of(rng.integers(0, 2, n))
+    np.testing.assert_array_equal(oracle.modified_hash(n, m, s, a ^ b),
+                                  oracle.modified_hash(n, m, s, a) ^ oracle.modified_hash(n, m, s, b))
