@@ -311,6 +311,52 @@ def measure_long_block(pa, inputs, torch, dev, reps=3):
     return res
 
 
+def measure_modified(pa, inputs, torch, dev, steps=20):
+    """The modified Toeplitz hash [I_m, T'] (Eq. 2-3) on the same DV-QKD batches (64 keys per (n, m),
+    one seed of n-1 bits each): one step issues the six batches, then runs their guard steps."""
+    stream = torch.cuda.current_stream()
+    cases = []
+    for n, m in subconfigs():
+        seed = inputs.bernoulli_bits(0, inputs.STREAM_SEED, n - 1)
+        keys = inputs.batch_keys(n, NKEYS, base_seed=0)
+        kw = keys.shape[1] + (keys.shape[1] & 1)
+        kb = np.zeros((NKEYS, kw), np.uint64)
+        kb[:, : keys.shape[1]] = keys
+        ow = (m + 63) // 64
+        ow += ow & 1
+        plan = pa.Plan(n, m, pa.PA_FP32_GUARD, modified=True)
+        plan.set_seed(_dev_words(torch, seed, dev))
+        cases.append(dict(n=n, plan=plan, kw=kw, ow=ow, dk=torch.from_numpy(kb.view(np.int64)).to(dev),
+                          out=torch.empty((NKEYS, ow), dtype=torch.int64, device=dev)))
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        for c in cases:
+            pa.pa_hash_batch_async(c["plan"].handle, c["dk"], NKEYS, c["kw"], c["out"], c["ow"], stream)
+        for c in cases:
+            pa.pa_batch_finish(c["plan"].handle)
+
+    for _ in range(3):
+        step()
+    ts = []
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    ms = statistics.mean(ts)
+    bits = sum(c["n"] for c in cases) * NKEYS
+    res = {"value": bits / (ms * 1e-3) / 1e6, "unit": "Mbit/s", "ms_per_step": ms, "mode": "FP32_GUARD",
+           "transform_lengths": [c["plan"].shape()[0] for c in cases]}
+    for c in cases:
+        c["plan"].close()
+    return res
+
+
 def run_ours(args):
     import torch
     import paper_1809_07592_gb300 as pa
@@ -486,6 +532,7 @@ def run_ours(args):
         extra["uneven_256_blocks"] = measure_uneven(pa, inputs, torch, dev)
         extra["serving"] = measure_serving(pa, inputs, torch, dev)
         extra["long_block_2p27"] = measure_long_block(pa, inputs, torch, dev)
+        extra["modified_toeplitz"] = measure_modified(pa, inputs, torch, dev)
 
     if rank == 0:
         lat_sorted = sorted(lat_ms)

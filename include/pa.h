@@ -106,6 +106,18 @@ int pa_plan_splits(uint64_t n, uint64_t m, pa_dtype_t dtype, uint32_t *L1, uint3
  */
 int pa_plan_split(uint64_t n, uint64_t m, pa_dtype_t dtype, uint32_t L1, uint32_t L2, uint32_t L3, pa_plan_t **out);
 
+/*
+ * pa_plan_modified -- plan for the modified Toeplitz hash of Section 2.2 (Eq. 2-3):
+ * the m x n matrix [I_m, T'] with T' the m x (n-m) Toeplitz block
+ * T'[i][j] = s[i - j + n - m - 1] of an (n-1)-bit seed s, so that
+ *     y_i = x_i XOR (XOR_{j < n-m} s[i - j + n - m - 1] AND x_{m+j}),   0 <= i < m.
+ * (The paper prints the block as V_{r-1-i+j}: the same map with the seed reversed.)
+ * The transform length only has to cover n-1 instead of n+m-1. Use the plan with
+ * pa_set_seed (seed_bits = n - 1), pa_hash_batch / pa_hash_host and their async
+ * forms exactly as a pa_plan plan; keys are n bits. 1 <= m < n <= 2^27.
+ */
+int pa_plan_modified(uint64_t n, uint64_t m, pa_dtype_t dtype, pa_plan_t **out);
+
 /* Release a plan and all device memory it owns. NULL is accepted. Synchronizes the device. */
 int pa_plan_destroy(pa_plan_t *plan);
 

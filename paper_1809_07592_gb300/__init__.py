@@ -106,6 +106,7 @@ def lib():
     L.pa_plan_splits.argtypes = [u64, u64, ctypes.c_int, ctypes.POINTER(u32), ctypes.POINTER(u32),
                                  ctypes.POINTER(u32), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     L.pa_plan_split.argtypes = [u64, u64, ctypes.c_int, u32, u32, u32, ctypes.POINTER(vp)]
+    L.pa_plan_modified.argtypes = [u64, u64, ctypes.c_int, ctypes.POINTER(vp)]
     L.pa_profile_enable.argtypes = [vp, ctypes.c_int]
     L.pa_profile_read.argtypes = [vp, ctypes.POINTER(KernelStat), ctypes.POINTER(ctypes.c_int), ctypes.c_int]
     bdp = ctypes.POINTER(BlockDesc)
@@ -129,7 +130,7 @@ def lib():
     L.pa_last_cuda_error.restype = ctypes.c_char_p
     for name in ("pa_plan", "pa_plan_destroy", "pa_set_seed", "pa_hash_batch", "pa_hash_batch_async",
                  "pa_batch_finish", "pa_hash_host_async", "pa_hash_host", "pa_plan_set_guard",
-                 "pa_plan_shape", "pa_plan_splits", "pa_plan_split", "pa_profile_enable", "pa_profile_read", "pa_uneven_create", "pa_uneven_update",
+                 "pa_plan_shape", "pa_plan_splits", "pa_plan_split", "pa_plan_modified", "pa_profile_enable", "pa_profile_read", "pa_uneven_create", "pa_uneven_update",
                  "pa_uneven_run", "pa_uneven_set_guard", "pa_uneven_destroy", "pa_uneven_class", "pa_hash_uneven",
                  "pa_server_create", "pa_submit", "pa_poll", "pa_wait", "pa_server_stats", "pa_server_destroy"):
         getattr(L, name).restype = ctypes.c_int
@@ -187,6 +188,15 @@ def pa_plan_split(n: int, m: int, dtype, split) -> int:
         dtype = DTYPES[dtype]
     h = ctypes.c_void_p()
     _check(lib().pa_plan_split(n, m, dtype, split[0], split[1], split[2], ctypes.byref(h)), "pa_plan_split")
+    return h.value
+
+
+def pa_plan_modified(n: int, m: int, dtype=PA_FP32_GUARD) -> int:
+    """Plan for the modified Toeplitz hash [I_m, T'] (keys of n bits, seeds of n-1 bits)."""
+    if isinstance(dtype, str):
+        dtype = DTYPES[dtype]
+    h = ctypes.c_void_p()
+    _check(lib().pa_plan_modified(n, m, dtype, ctypes.byref(h)), "pa_plan_modified")
     return h.value
 
 
@@ -399,9 +409,15 @@ def pa_server_destroy(server: int) -> None:
 class Plan:
     """Owns one pa_plan handle; a convenience wrapper over the functions above."""
 
-    def __init__(self, n: int, m: int, dtype=PA_FP32_GUARD, split=None):
-        self.n, self.m = n, m
-        self.handle = pa_plan(n, m, dtype) if split is None else pa_plan_split(n, m, dtype, split)
+    def __init__(self, n: int, m: int, dtype=PA_FP32_GUARD, split=None, modified: bool = False):
+        self.n, self.m, self.modified = n, m, modified
+        if modified:
+            self.handle = pa_plan_modified(n, m, dtype)
+        else:
+            self.handle = pa_plan(n, m, dtype) if split is None else pa_plan_split(n, m, dtype, split)
+
+    def seed_bits(self) -> int:
+        return self.n - 1 if self.modified else self.n + self.m - 1
 
     def words_in(self) -> int:
         return (self.n + 63) // 64
@@ -410,7 +426,7 @@ class Plan:
         return (self.m + 63) // 64
 
     def set_seed(self, seed, stream=None):
-        pa_set_seed(self.handle, seed, self.n + self.m - 1, stream)
+        pa_set_seed(self.handle, seed, self.seed_bits(), stream)
 
     def hash(self, keys, out=None, stream=None, info=False):
         """keys: (nkeys, stride) int64 CUDA tensor (stride even or nkeys == 1)."""

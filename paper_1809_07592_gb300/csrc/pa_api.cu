@@ -71,7 +71,10 @@ struct PendingBatch {
 };
 
 struct pa_plan {
-    uint64_t n = 0, m = 0;
+    uint64_t n = 0, m = 0;   // the Toeplitz block: m outputs from n transform inputs
+    uint64_t n_key = 0;      // key length in bits (n, or n + m for the modified hash)
+    uint64_t koff = 0;       // first key bit of the Toeplitz block's input (0, or m)
+    bool modified = false;   // modified Toeplitz hash [I_m, T] (Section 2.2, Eq. 2-3)
     pa_dtype_t dtype = PA_FP64;
     int device = 0;
     uint64_t L = 0;
@@ -359,7 +362,7 @@ int run_keys(pa_plan_t *p, const uint64_t *keys, uint32_t nkeys, uint64_t kstrid
         const uint32_t nk = (nkeys - k0 < 2 * pairs) ? nkeys - k0 : 2 * pairs;
         const uint64_t *kp = keys + (uint64_t)k0 * kstride;
         uint64_t *op = out + (uint64_t)k0 * ostride;
-        { Timed t_(p, K_FWD_KEYS, st); PA_CUDA(launch_fwd_keys<T>(g.lg1, kp, nk, kstride, p->n, W, p->L, pairs, tw, popc + k0, st)); }
+        { Timed t_(p, K_FWD_KEYS, st); PA_CUDA(launch_fwd_keys<T>(g.lg1, kp, nk, kstride, p->n, W, p->L, pairs, tw, popc + k0, st, p->koff)); }
         if (g.lgM) {
             { Timed t_(p, K_MID_FWD, st); PA_CUDA(launch_mid<T>(g.lgM, false, W, p->L, g.inner(), pairs, tw, st)); }
             { Timed t_(p, K_MIDDLE_CONV, st); PA_CUDA(launch_middle<T>(g.ro, g.lgI, 0, W, spec, p->L, pairs, tw, one<T>(), st, p->err)); }
@@ -368,7 +371,7 @@ int run_keys(pa_plan_t *p, const uint64_t *keys, uint32_t nkeys, uint64_t kstrid
             Timed t_(p, K_MIDDLE_CONV, st);
             PA_CUDA(launch_middle<T>(g.ro, g.lgI, 0, W, spec, p->L, pairs, tw, one<T>(), st, p->err));
         }
-        { Timed t_(p, K_INV_BITS, st); PA_CUDA(launch_inv_bits<T>(g.lg1, W, p->L, p->m, nk, popc + k0, marg + k0, op, ostride, pairs, tw, st)); }
+        { Timed t_(p, K_INV_BITS, st); PA_CUDA(launch_inv_bits<T>(g.lg1, W, p->L, p->m, nk, popc + k0, marg + k0, op, ostride, pairs, tw, st, p->modified ? kp : nullptr, kstride)); }
     }
     return PA_OK;
 }
@@ -400,6 +403,12 @@ void free_plan(pa_plan_t *p) {
 
 bool plan_args_ok(uint64_t n, uint64_t m, pa_dtype_t dtype) {
     if (n == 0 || m == 0 || m > n || n > (1ull << 27)) return false;
+    return dtype == PA_FP64 || dtype == PA_FP32_GUARD || dtype == PA_NTT64;
+}
+
+// Modified hash: key of n bits, identity block m x m, Toeplitz block m x (n - m); 1 <= m < n.
+bool modified_args_ok(uint64_t n, uint64_t m, pa_dtype_t dtype) {
+    if (m == 0 || m >= n || n > (1ull << 27)) return false;
     return dtype == PA_FP64 || dtype == PA_FP32_GUARD || dtype == PA_NTT64;
 }
 
@@ -474,7 +483,7 @@ int tune_split(pa_plan_t *p, const std::vector<Geometry> &cand) {
     if (pairs > 32) pairs = 32;
     if (pairs > p->max_chunk_pairs) pairs = p->max_chunk_pairs;
     const uint32_t nkeys = 2 * pairs;
-    const uint64_t kw = ((p->n + 63) / 64 + 1) & ~1ull, ow = ((p->m + 63) / 64 + 1) & ~1ull;
+    const uint64_t kw = ((p->n_key + 63) / 64 + 1) & ~1ull, ow = ((p->m + 63) / 64 + 1) & ~1ull;
     uint64_t *keys = nullptr, *out = nullptr;
     cudaStream_t st = nullptr;
     cudaEvent_t a = nullptr, b = nullptr;
@@ -528,20 +537,25 @@ int tune_split(pa_plan_t *p, const std::vector<Geometry> &cand) {
     return fail(PA_OK);
 }
 
-// pa_plan, with the split forced when `force` is given.
-int plan_create(uint64_t n, uint64_t m, pa_dtype_t dtype, const Geometry *force, pa_plan_t **out) {
+// pa_plan (or pa_plan_modified), with the split forced when `force` is given. For the
+// modified hash, n is the key length and the Toeplitz block is m x (n - m).
+int plan_create(uint64_t n, uint64_t m, pa_dtype_t dtype, const Geometry *force, pa_plan_t **out,
+                bool modified = false) {
     if (!out) return PA_EINVAL;
     *out = nullptr;
-    if (!plan_args_ok(n, m, dtype)) return PA_EINVAL;
+    if (modified ? !modified_args_ok(n, m, dtype) : !plan_args_ok(n, m, dtype)) return PA_EINVAL;
     pa_plan_t *p = new pa_plan_t();
-    p->n = n;
+    p->modified = modified;
+    p->n_key = n;
+    p->koff = modified ? m : 0;
+    p->n = modified ? n - m : n;
     p->m = m;
     p->dtype = dtype;
     if (cudaGetDevice(&p->device) != cudaSuccess) {
         delete p;
         return cuda_fail(cudaGetLastError(), "cudaGetDevice");
     }
-    const Geometry geo = force ? *force : choose_geometry(n + m - 1, dtype, false);
+    const Geometry geo = force ? *force : choose_geometry(p->n + m - 1, dtype, false);
     if (geo.L == 0) {
         delete p;
         return PA_EUNSUPPORTED;
@@ -688,6 +702,10 @@ int pa_plan(uint64_t n, uint64_t m, pa_dtype_t dtype, pa_plan_t **out) {
     return plan_create(n, m, dtype, nullptr, out);
 }
 
+int pa_plan_modified(uint64_t n, uint64_t m, pa_dtype_t dtype, pa_plan_t **out) {
+    return plan_create(n, m, dtype, nullptr, out, true);
+}
+
 int pa_plan_splits(uint64_t n, uint64_t m, pa_dtype_t dtype, uint32_t *L1, uint32_t *L2, uint32_t *L3, int cap,
                    int *count) {
     if (!count || cap < 0 || (cap > 0 && (!L1 || !L2 || !L3))) return PA_EINVAL;
@@ -796,7 +814,7 @@ int pa_hash_batch_async(pa_plan_t *p, const uint64_t *keys_dev, uint32_t nkeys, 
                         uint64_t *out_dev, uint64_t out_stride_words, pa_stream_t stream) {
     if (!p || !keys_dev || !out_dev || nkeys == 0) return PA_EINVAL;
     if (!aligned16(keys_dev) || !aligned16(out_dev)) return PA_EINVAL;
-    if (key_stride_words < (p->n + 63) / 64 || out_stride_words < (p->m + 63) / 64) return PA_EINVAL;
+    if (key_stride_words < (p->n_key + 63) / 64 || out_stride_words < (p->m + 63) / 64) return PA_EINVAL;
     if ((nkeys > 1 && (key_stride_words & 1)) || (nkeys > 1 && (out_stride_words & 1))) return PA_EINVAL;
     if (!p->seeded) return PA_ENOSEED;
     std::lock_guard<std::mutex> lk(p->mu);
@@ -822,7 +840,7 @@ int pa_hash_batch_async(pa_plan_t *p, const uint64_t *keys_dev, uint32_t nkeys, 
 int pa_hash_host_async(pa_plan_t *p, const uint64_t *keys_host, uint32_t nkeys, uint64_t key_stride_words,
                        uint64_t *out_host, uint64_t out_stride_words, pa_stream_t stream) {
     if (!p || !keys_host || !out_host || nkeys == 0) return PA_EINVAL;
-    const uint64_t kw = (p->n + 63) / 64, ow = (p->m + 63) / 64;
+    const uint64_t kw = (p->n_key + 63) / 64, ow = (p->m + 63) / 64;
     if (key_stride_words < kw || out_stride_words < ow) return PA_EINVAL;
     if (!p->seeded) return PA_ENOSEED;
     std::lock_guard<std::mutex> lk(p->mu);
@@ -892,7 +910,7 @@ int pa_batch_finish(pa_plan_t *p, pa_batch_info_t *info) {
             // inside the FP64 plan when its own margin fails).
             if (!p->fallback) {
                 pa_plan_t *fb = nullptr;
-                int rc = pa_plan(p->n, p->m, PA_FP64, &fb);
+                int rc = plan_create(p->n_key, p->m, PA_FP64, nullptr, &fb, p->modified);
                 if (rc != PA_OK) return rc;
                 p->fallback = fb;
             }
@@ -902,7 +920,7 @@ int pa_batch_finish(pa_plan_t *p, pa_batch_info_t *info) {
         } else if (p->dtype == PA_FP64 && !(mk_ <= p->guard)) {
             if (!p->fallback) {
                 pa_plan_t *fb = nullptr;
-                int rc = pa_plan(p->n, p->m, PA_NTT64, &fb);
+                int rc = plan_create(p->n_key, p->m, PA_NTT64, nullptr, &fb, p->modified);
                 if (rc != PA_OK) return rc;
                 p->fallback = fb;
             }

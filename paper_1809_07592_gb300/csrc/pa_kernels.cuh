@@ -137,7 +137,7 @@ __device__ __forceinline__ uint32_t bits_at(const uint64_t *v, uint64_t nbits, u
 template <typename T, int LEN, int COLS, int E>
 __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
     k_fwd_keys(const uint64_t *__restrict__ keys, uint32_t nkeys, uint64_t kstride, uint64_t n,
-               cx<T> *__restrict__ W, uint64_t L, TwTab<T> tw, uint32_t *__restrict__ popc) {
+               cx<T> *__restrict__ W, uint64_t L, TwTab<T> tw, uint32_t *__restrict__ popc, uint64_t koff) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T> *sm = reinterpret_cast<cx<T> *>(smem_raw);
     const uint32_t col = threadIdx.x % COLS, tq = threadIdx.x / COLS;
@@ -150,10 +150,21 @@ __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
     uint32_t *stage = key_stage<T, LEN, COLS>(smem_raw);
     const uint64_t u0 = (uint64_t)blockIdx.x * COLS;
     uint32_t ca = 0, cb = 0;  // the CTA's share of each key's popcount P (the CTAs tile every bit once)
+    // The transform's input element t is key bit koff + t (koff = 0, or m for the modified
+    // Toeplitz hash, whose Toeplitz block multiplies key bits m .. n-1).
+    const uint64_t nk = n + koff;
+    const bool aligned = (koff % COLS) == 0;
+    const uint64_t *xa = keys + (uint64_t)(2 * pair) * kstride, *xb = xa + kstride;
     for (uint32_t a = threadIdx.x; a < LEN; a += blockDim.x) {
-        const uint64_t t0 = (uint64_t)a * S + u0;  // S % 64 == 0: the COLS bits sit in one word
-        const uint32_t wa = aligned_bits<COLS>(keys + (uint64_t)(2 * pair) * kstride, n, t0);
-        const uint32_t wb = has_b ? aligned_bits<COLS>(keys + (uint64_t)(2 * pair + 1) * kstride, n, t0) : 0u;
+        const uint64_t t0 = (uint64_t)a * S + u0 + koff;  // S % 64 == 0: aligned COLS bits sit in one word
+        uint32_t wa, wb = 0u;
+        if (aligned) {
+            wa = aligned_bits<COLS>(xa, nk, t0);
+            if (has_b) wb = aligned_bits<COLS>(xb, nk, t0);
+        } else {
+            wa = bits_at(xa, nk, t0, COLS);
+            if (has_b) wb = bits_at(xb, nk, t0, COLS);
+        }
         stage[a] = wa | (wb << 16);
         ca += __popc(wa);
         cb += __popc(wb);
@@ -395,7 +406,7 @@ template <typename T, int LEN, int COLS, int E>
 __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
     k_inv_bits(const cx<T> *__restrict__ W, uint64_t L, uint64_t m, uint32_t nkeys,
                const uint32_t *__restrict__ popc, uint32_t *__restrict__ margin_bits, uint64_t *__restrict__ out,
-               uint64_t ostride, TwTab<T> tw) {
+               uint64_t ostride, TwTab<T> tw, const uint64_t *__restrict__ xkeys, uint64_t xstride) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T> *sm = reinterpret_cast<cx<T> *>(smem_raw);
     using word_t = typename BitsWord<COLS>::type;
@@ -434,8 +445,13 @@ __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
         if (col == 0 && ci < nchunks) {
             const uint32_t sh = lane;  // lane = group * COLS
             const uint32_t msk = (COLS == 32) ? 0xffffffffu : ((1u << COLS) - 1u);
-            oa[ci] = (word_t)((ba >> sh) & msk);
-            if (has_b) ob[ci] = (word_t)((bb >> sh) & msk);
+            uint32_t ya = (ba >> sh) & msk, yb = (bb >> sh) & msk;
+            if (xkeys) {  // modified Toeplitz hash (Eq. 3): the identity block adds key bits 0 .. m-1
+                ya ^= aligned_bits<COLS>(xkeys + (uint64_t)ka * xstride, m, ci * COLS);
+                if (has_b) yb ^= aligned_bits<COLS>(xkeys + (uint64_t)kb * xstride, m, ci * COLS);
+            }
+            oa[ci] = (word_t)ya;
+            if (has_b) ob[ci] = (word_t)yb;
         }
     }
     uint32_t fa = __float_as_uint(margin_to_float(ma)), fb = __float_as_uint(margin_to_float(mb));

@@ -44,7 +44,8 @@ static cudaError_t by_len(int lg, F &&f) {
 
 template <typename T>
 cudaError_t launch_fwd_keys(int lgLEN, const uint64_t *keys, uint32_t nkeys, uint64_t kstride, uint64_t n,
-                            cx<T> *W, uint64_t L, uint32_t pairs, TwTab<T> tw, uint32_t *popc, cudaStream_t st) {
+                            cx<T> *W, uint64_t L, uint32_t pairs, TwTab<T> tw, uint32_t *popc, cudaStream_t st,
+                            uint64_t koff) {
     constexpr int E = Shape<T>::E, COLS = Shape<T>::COLS;
     return by_len<kMinLgStrided, kMaxLgStrided>(lgLEN, [&](auto c) {
         constexpr int LEN = decltype(c)::value;
@@ -53,7 +54,7 @@ cudaError_t launch_fwd_keys(int lgLEN, const uint64_t *keys, uint32_t nkeys, uin
         cudaError_t e = set_smem(kern, sb);
         if (e != cudaSuccess) return e;
         dim3 grid((unsigned)((L / LEN) / COLS), pairs);
-        kern<<<grid, COLS * LEN / E, sb, st>>>(keys, nkeys, kstride, n, W, L, tw, popc);
+        kern<<<grid, COLS * LEN / E, sb, st>>>(keys, nkeys, kstride, n, W, L, tw, popc, koff);
         return cudaGetLastError();
     });
 }
@@ -218,7 +219,8 @@ cudaError_t launch_middle_odd(int lg, int mode, cx<T> *W, cx<T> *spec, uint64_t 
 template <typename T>
 cudaError_t launch_inv_bits(int lgLEN, const cx<T> *W, uint64_t L, uint64_t m, uint32_t nkeys,
                             const uint32_t *popc, uint32_t *margin_bits, uint64_t *out, uint64_t ostride,
-                            uint32_t pairs, TwTab<T> tw, cudaStream_t st) {
+                            uint32_t pairs, TwTab<T> tw, cudaStream_t st, const uint64_t *xkeys,
+                            uint64_t xstride) {
     constexpr int E = Shape<T>::E, COLS = Shape<T>::COLS;
     return by_len<kMinLgStrided, kMaxLgStrided>(lgLEN, [&](auto c) {
         constexpr int LEN = decltype(c)::value;
@@ -227,14 +229,14 @@ cudaError_t launch_inv_bits(int lgLEN, const cx<T> *W, uint64_t L, uint64_t m, u
         cudaError_t e = set_smem(kern, sb);
         if (e != cudaSuccess) return e;
         dim3 grid((unsigned)((L / LEN) / COLS), pairs);
-        kern<<<grid, COLS * LEN / E, sb, st>>>(W, L, m, nkeys, popc, margin_bits, out, ostride, tw);
+        kern<<<grid, COLS * LEN / E, sb, st>>>(W, L, m, nkeys, popc, margin_bits, out, ostride, tw, xkeys, xstride);
         return cudaGetLastError();
     });
 }
 
 #define PA_INSTANTIATE_LAUNCHERS(T)                                                                              \
     template cudaError_t launch_fwd_keys<T>(int, const uint64_t *, uint32_t, uint64_t, uint64_t, cx<T> *,        \
-                                            uint64_t, uint32_t, TwTab<T>, uint32_t *, cudaStream_t);             \
+                                            uint64_t, uint32_t, TwTab<T>, uint32_t *, cudaStream_t, uint64_t);   \
     template cudaError_t launch_fwd_seed<T>(int, const uint64_t *, uint64_t, uint64_t, cx<T> *, uint64_t,        \
                                             TwTab<T>, cudaStream_t);                                             \
     template cudaError_t launch_mid<T>(int, bool, cx<T> *, uint64_t, uint32_t, uint32_t, TwTab<T>,               \
@@ -242,7 +244,8 @@ cudaError_t launch_inv_bits(int lgLEN, const cx<T> *W, uint64_t L, uint64_t m, u
     template cudaError_t launch_middle<T>(int, int, int, cx<T> *, cx<T> *, uint64_t, uint32_t, TwTab<T>, cx<T>,  \
                                           cudaStream_t, uint32_t *);                                            \
     template cudaError_t launch_inv_bits<T>(int, const cx<T> *, uint64_t, uint64_t, uint32_t, const uint32_t *,  \
-                                            uint32_t *, uint64_t *, uint64_t, uint32_t, TwTab<T>, cudaStream_t);
+                                            uint32_t *, uint64_t *, uint64_t, uint32_t, TwTab<T>, cudaStream_t,  \
+                                            const uint64_t *, uint64_t);
 
 template <typename T>
 cudaError_t launch_fwd_keyseed(int lgLEN, const BlockDev *blocks, uint32_t nblocks, cx<T> *W, uint64_t L,

@@ -35,10 +35,12 @@ constexpr int kMinLgMiddle = 6;
 cudaError_t launch_zero_keys(uint32_t nkeys, uint32_t *popc, uint32_t *margin_bits, cudaStream_t st);
 
 // Level-1 forward pass of key pairs; also adds each key's popcount into popc[k]
-// (which must be zero beforehand: launch_zero_keys).
+// (which must be zero beforehand: launch_zero_keys). The transform input is key
+// bits koff .. koff+n-1 (koff = m for the modified Toeplitz hash).
 template <typename T>
 cudaError_t launch_fwd_keys(int lgLEN, const uint64_t *keys, uint32_t nkeys, uint64_t kstride, uint64_t n,
-                            cx<T> *W, uint64_t L, uint32_t pairs, TwTab<T> tw, uint32_t *popc, cudaStream_t st);
+                            cx<T> *W, uint64_t L, uint32_t pairs, TwTab<T> tw, uint32_t *popc, cudaStream_t st,
+                            uint64_t koff = 0);
 template <typename T>
 cudaError_t launch_fwd_seed(int lgLEN, const uint64_t *seed, uint64_t n, uint64_t m, cx<T> *W, uint64_t L,
                             TwTab<T> tw, cudaStream_t st);
@@ -64,10 +66,13 @@ template <typename T>
 constexpr bool odd_inner_ok(int ro, int lg, bool split) {
     return lg >= kMinLgOdd && lg <= kMaxLgOdd && (long long)ro * (1ll << lg) / Shape<T>::E <= (split ? 512 : 1024);
 }
+// Level-1 inverse pass with the bit output. With xkeys, output bit i of key k is
+// XORed with bit i of xkeys + k*xstride (the identity block of the modified hash).
 template <typename T>
 cudaError_t launch_inv_bits(int lgLEN, const cx<T> *W, uint64_t L, uint64_t m, uint32_t nkeys,
                             const uint32_t *popc, uint32_t *margin_bits, uint64_t *out, uint64_t ostride,
-                            uint32_t pairs, TwTab<T> tw, cudaStream_t st);
+                            uint32_t pairs, TwTab<T> tw, cudaStream_t st, const uint64_t *xkeys = nullptr,
+                            uint64_t xstride = 0);
 
 // ---- uneven batch (complex arithmetic only: the Eq. 5-10 split needs conjugation) ----
 struct BlockDev;
