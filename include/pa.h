@@ -107,6 +107,19 @@ int pa_plan_splits(uint64_t n, uint64_t m, pa_dtype_t dtype, uint32_t *L1, uint3
 int pa_plan_split(uint64_t n, uint64_t m, pa_dtype_t dtype, uint32_t L1, uint32_t L2, uint32_t L3, pa_plan_t **out);
 
 /*
+ * Security parameter of the hash (paper Section 2.1, Eq. 1). If Eve holds at most t
+ * bits of information about the n-bit reconciled key, hashing it to r bits with a
+ * universal (Toeplitz) hash leaves her I(K; g, V) <= 2^-s / ln 2 bits about the
+ * final key, with security coefficient s = n - t - r.
+ * pa_final_key_length: r = n - t - s for a wanted s; PA_EINVAL unless r >= 1
+ *   (t < n and s < n - t). Host only.
+ * pa_leakage_bound: the right-hand side 2^-(n-t-r) / ln 2 of Eq. 1 (for n - t - r <= 0
+ *   the value is >= 1/ln 2, i.e. no guarantee). Host only.
+ */
+int pa_final_key_length(uint64_t n, uint64_t t, uint64_t s, uint64_t *r);
+double pa_leakage_bound(uint64_t n, uint64_t t, uint64_t r);
+
+/*
  * pa_plan_modified -- plan for the modified Toeplitz hash of Section 2.2 (Eq. 2-3):
  * the m x n matrix [I_m, T'] with T' the m x (n-m) Toeplitz block
  * T'[i][j] = s[i - j + n - m - 1] of an (n-1)-bit seed s, so that

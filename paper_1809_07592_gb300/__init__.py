@@ -107,6 +107,10 @@ def lib():
                                  ctypes.POINTER(u32), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     L.pa_plan_split.argtypes = [u64, u64, ctypes.c_int, u32, u32, u32, ctypes.POINTER(vp)]
     L.pa_plan_modified.argtypes = [u64, u64, ctypes.c_int, ctypes.POINTER(vp)]
+    L.pa_final_key_length.argtypes = [u64, u64, u64, ctypes.POINTER(u64)]
+    L.pa_final_key_length.restype = ctypes.c_int
+    L.pa_leakage_bound.argtypes = [u64, u64, u64]
+    L.pa_leakage_bound.restype = ctypes.c_double
     L.pa_profile_enable.argtypes = [vp, ctypes.c_int]
     L.pa_profile_read.argtypes = [vp, ctypes.POINTER(KernelStat), ctypes.POINTER(ctypes.c_int), ctypes.c_int]
     bdp = ctypes.POINTER(BlockDesc)
@@ -189,6 +193,18 @@ def pa_plan_split(n: int, m: int, dtype, split) -> int:
     h = ctypes.c_void_p()
     _check(lib().pa_plan_split(n, m, dtype, split[0], split[1], split[2], ctypes.byref(h)), "pa_plan_split")
     return h.value
+
+
+def pa_final_key_length(n: int, t: int, s: int) -> int:
+    """Eq. 1: final key length r = n - t - s for Eve's information t and security coefficient s."""
+    r = ctypes.c_uint64()
+    _check(lib().pa_final_key_length(n, t, s, ctypes.byref(r)), "pa_final_key_length")
+    return r.value
+
+
+def pa_leakage_bound(n: int, t: int, r: int) -> float:
+    """Eq. 1: upper bound 2^-(n-t-r)/ln 2 on Eve's information about the r-bit final key."""
+    return lib().pa_leakage_bound(n, t, r)
 
 
 def pa_plan_modified(n: int, m: int, dtype=PA_FP32_GUARD) -> int:

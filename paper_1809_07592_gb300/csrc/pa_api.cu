@@ -702,6 +702,20 @@ int pa_plan(uint64_t n, uint64_t m, pa_dtype_t dtype, pa_plan_t **out) {
     return plan_create(n, m, dtype, nullptr, out);
 }
 
+int pa_final_key_length(uint64_t n, uint64_t t, uint64_t s, uint64_t *r) {
+    if (!r) return PA_EINVAL;
+    *r = 0;
+    if (t >= n || s >= n - t) return PA_EINVAL;  // Eq. 1 needs r = n - t - s >= 1
+    *r = n - t - s;
+    return PA_OK;
+}
+
+double pa_leakage_bound(uint64_t n, uint64_t t, uint64_t r) {
+    // Eq. 1: I(K; g, V) <= 2^-s / ln 2 with s = n - t - r (may be <= 0: then the bound is >= 1/ln 2)
+    const double s = (double)n - (double)t - (double)r;
+    return std::exp2(-s) / std::log(2.0);
+}
+
 int pa_plan_modified(uint64_t n, uint64_t m, pa_dtype_t dtype, pa_plan_t **out) {
     return plan_create(n, m, dtype, nullptr, out, true);
 }

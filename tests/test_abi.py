@@ -65,3 +65,22 @@ def test_split_listing_without_gpu():
         raise AssertionError("m > n accepted")
     except pa.PAError as e:
         assert e.code == pa.PA_EINVAL
+
+
+def test_security_parameter_helpers_without_gpu():
+    """Eq. 1: r = n - t - s and the bound 2^-s / ln 2 (host-only entry points)."""
+    import math
+    import paper_1809_07592_gb300 as pa
+    build.build()
+    assert pa.pa_final_key_length(1_000_000, 400_000, 100) == 599_900
+    assert pa.pa_final_key_length(10, 0, 9) == 1
+    for n, t, s in [(10, 10, 0), (10, 3, 7), (10, 11, 0), (0, 0, 0)]:
+        try:
+            pa.pa_final_key_length(n, t, s)
+            raise AssertionError((n, t, s))
+        except pa.PAError as e:
+            assert e.code == pa.PA_EINVAL
+    assert math.isclose(pa.pa_leakage_bound(1000, 400, 500), 2.0 ** -100 / math.log(2), rel_tol=1e-12)
+    assert math.isclose(pa.pa_leakage_bound(1000, 400, 600), 1 / math.log(2), rel_tol=1e-12)
+    # the bound halves for every bit dropped from the final key
+    assert math.isclose(pa.pa_leakage_bound(5000, 1000, 3900) / pa.pa_leakage_bound(5000, 1000, 3901), 0.5)
