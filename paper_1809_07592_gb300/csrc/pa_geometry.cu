@@ -49,9 +49,10 @@ std::vector<Geometry> geometry_candidates(uint64_t L, pa_dtype_t dtype, bool spl
     for (int lg1 = kMinLgStrided; lg1 <= kMaxLgStrided; ++lg1) {
         const int lgI2 = k - lg1;
         if (lgI2 >= 0 && inner_valid(dtype, ro, lgI2, split)) two.push_back(Geometry{L, lg1, 0, ro, lgI2});
-        const int lgI3 = k - lg1 - kMinLgStrided;
-        if (lgI3 >= 0 && inner_valid(dtype, ro, lgI3, split))
-            three.push_back(Geometry{L, lg1, kMinLgStrided, ro, lgI3});
+        for (int lgM = kMinLgStrided; lgM <= kMaxLgStrided; ++lgM) {
+            const int lgI3 = k - lg1 - lgM;
+            if (lgI3 >= 0 && inner_valid(dtype, ro, lgI3, split)) three.push_back(Geometry{L, lg1, lgM, ro, lgI3});
+        }
     }
     return two.empty() ? three : two;
 }

@@ -484,14 +484,11 @@ struct BlockDev {
     uint32_t pad;
 };
 
-// popcount of each block's key and margin reset (one CTA per block of the class).
-__global__ void k_prep_blocks(const BlockDev *__restrict__ blocks, uint32_t *__restrict__ popc,
-                              uint32_t *__restrict__ margin_bits);
-
 // Level-1 forward pass of z = x + i*sigma for every block of a class. Grid (S/COLS, blocks).
 template <typename T, int LEN, int COLS, int E>
 __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
-    k_fwd_keyseed(const BlockDev *__restrict__ blocks, cx<T> *__restrict__ W, uint64_t L, TwTab<T> tw) {
+    k_fwd_keyseed(const BlockDev *__restrict__ blocks, cx<T> *__restrict__ W, uint64_t L, TwTab<T> tw,
+                  uint32_t *__restrict__ popc) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T> *sm = reinterpret_cast<cx<T> *>(smem_raw);
     const uint32_t col = threadIdx.x % COLS, tq = threadIdx.x / COLS;
@@ -505,9 +502,11 @@ __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
     uint64_t *stage = reinterpret_cast<uint64_t *>(key_stage<T, LEN, COLS>(smem_raw));
     const uint64_t u0 = (uint64_t)blockIdx.x * COLS;
     const uint32_t full = (1u << COLS) - 1u;
+    uint32_t ck = 0;  // the CTA's share of the key's popcount P (the CTAs tile every bit once)
     for (uint32_t a = threadIdx.x; a < LEN; a += blockDim.x) {
         const uint64_t t0 = (uint64_t)a * S + u0;
         const uint32_t wk = aligned_bits<COLS>(bd.key, n, t0);
+        ck += __popc(wk);
         uint64_t j0 = t0 + n - 1;
         if (j0 >= L) j0 -= L;
         uint32_t ws, inr;
@@ -523,6 +522,8 @@ __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
         }
         stage[a] = (uint64_t)wk | ((uint64_t)ws << 16) | ((uint64_t)inr << 32);
     }
+    ck = __reduce_add_sync(0xffffffffu, ck);
+    if ((threadIdx.x & 31) == 0 && ck) atomicAdd(popc + bd.id, ck);
     __syncthreads();
     cx<T> v[E];
 #pragma unroll

@@ -79,7 +79,7 @@ template <typename T>
 cudaError_t launch_mid(int lgLEN, bool inverse, cx<T> *W, uint64_t L, uint32_t S, uint32_t pairs, TwTab<T> tw,
                        cudaStream_t st) {
     constexpr int E = Shape<T>::E, COLS = Shape<T>::COLS;
-    return by_len<kMinLgStrided, kMinLgStrided>(lgLEN, [&](auto c) {
+    return by_len<kMinLgStrided, kMaxLgStrided>(lgLEN, [&](auto c) {
         constexpr int LEN = decltype(c)::value;
         constexpr size_t sb = smem_bytes<T, LEN, COLS>();
         const uint64_t nblk = L / ((uint64_t)LEN * S);
@@ -249,7 +249,7 @@ cudaError_t launch_inv_bits(int lgLEN, const cx<T> *W, uint64_t L, uint64_t m, u
 
 template <typename T>
 cudaError_t launch_fwd_keyseed(int lgLEN, const BlockDev *blocks, uint32_t nblocks, cx<T> *W, uint64_t L,
-                               TwTab<T> tw, cudaStream_t st) {
+                               TwTab<T> tw, uint32_t *popc, cudaStream_t st) {
     constexpr int E = Shape<T>::E, COLS = Shape<T>::COLS;
     return by_len<kMinLgStrided, kMaxLgStrided>(lgLEN, [&](auto c) {
         constexpr int LEN = decltype(c)::value;
@@ -258,7 +258,7 @@ cudaError_t launch_fwd_keyseed(int lgLEN, const BlockDev *blocks, uint32_t nbloc
         cudaError_t e = set_smem(kern, sb);
         if (e != cudaSuccess) return e;
         dim3 grid((unsigned)((L / LEN) / COLS), nblocks);
-        kern<<<grid, COLS * LEN / E, sb, st>>>(blocks, W, L, tw);
+        kern<<<grid, COLS * LEN / E, sb, st>>>(blocks, W, L, tw, popc);
         return cudaGetLastError();
     });
 }
@@ -332,7 +332,7 @@ cudaError_t launch_inv_bits_blocks(int lgLEN, const cx<T> *Wi, uint64_t L, const
 
 #define PA_INSTANTIATE_UNEVEN(T)                                                                                 \
     template cudaError_t launch_fwd_keyseed<T>(int, const BlockDev *, uint32_t, cx<T> *, uint64_t, TwTab<T>,     \
-                                               cudaStream_t);                                                   \
+                                               uint32_t *, cudaStream_t);                                       \
     template cudaError_t launch_middle_split<T>(int, int, const cx<T> *, cx<T> *, uint64_t, uint32_t, uint32_t,  \
                                                 uint32_t, TwTab<T>, cudaStream_t);                               \
     template cudaError_t launch_inv_bits_blocks<T>(int, const cx<T> *, uint64_t, const BlockDev *, uint32_t,     \

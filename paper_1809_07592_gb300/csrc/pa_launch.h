@@ -80,11 +80,12 @@ template <typename T> struct MaxLgSplit;
 template <> struct MaxLgSplit<float> { static constexpr int v = 13; };
 template <> struct MaxLgSplit<double> { static constexpr int v = 12; };
 
-cudaError_t launch_prep_blocks(const BlockDev *blocks, uint32_t nblocks, uint32_t *popc, uint32_t *margin_bits,
+// Zero popc[id] and margin_bits[id] of every block (launch_fwd_keyseed accumulates the popcounts).
+cudaError_t launch_zero_blocks(const BlockDev *blocks, uint32_t nblocks, uint32_t *popc, uint32_t *margin_bits,
                                cudaStream_t st);
 template <typename T>
 cudaError_t launch_fwd_keyseed(int lgLEN, const BlockDev *blocks, uint32_t nblocks, cx<T> *W, uint64_t L,
-                               TwTab<T> tw, cudaStream_t st);
+                               TwTab<T> tw, uint32_t *popc, cudaStream_t st);
 template <typename T>
 cudaError_t launch_middle_split(int ro, int lg, const cx<T> *Wf, cx<T> *Wi, uint64_t L, uint32_t nblocks,
                                 uint32_t lgL1, uint32_t lgM, TwTab<T> tw, cudaStream_t st);

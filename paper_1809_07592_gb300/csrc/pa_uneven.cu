@@ -136,8 +136,8 @@ int run_class_complex(const ClassRun &c, uint32_t *popc, uint32_t *marg, cudaStr
     const uint32_t nb = c.nb;
     const TwTab<T> tw = tw_of<T>(c);
     cx<T> *Wf = static_cast<cx<T> *>(c.Wf), *Wi = static_cast<cx<T> *>(c.Wi);
-    U_CUDA(launch_prep_blocks(c.d_blocks, nb, popc, marg, st));
-    U_CUDA(launch_fwd_keyseed<T>(g.lg1, c.d_blocks, nb, Wf, g.L, tw, st));
+    U_CUDA(launch_zero_blocks(c.d_blocks, nb, popc, marg, st));
+    U_CUDA(launch_fwd_keyseed<T>(g.lg1, c.d_blocks, nb, Wf, g.L, tw, popc, st));
     if (g.lgM) {
         int rc = mid_chunks<T>(c, false, Wf, nb, st);
         if (rc != PA_OK) return rc;
