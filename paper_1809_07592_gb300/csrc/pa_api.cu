@@ -57,6 +57,17 @@ inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 
 
 }  // namespace
 
+// Single keys in a half-length transform (FP32 / FP64): one key of a length-2N
+// convolution as z[t] = x[2t] + i x[2t+1], split per bin pair (k, N-k) against
+// per-bin seed tables, so a lone key costs half the transform work of a key pair.
+struct RealMode {
+    Geometry geo;  // the length-N transform, N = geo.L
+    void *tw_hi = nullptr, *tw_lo = nullptr, *tw_fine = nullptr;
+    uint32_t twB = 0;
+    void *tabs = nullptr;  // 3N values: E_s, O_s, w_N^k O_s (times 1/N), digit-reversed bin order
+    bool seeded = false;
+};
+
 // The arguments of an issued batch, kept for its guard step.
 struct PendingBatch {
     bool active = false;
@@ -96,6 +107,7 @@ struct pa_plan {
     bool seeded = false;
     float guard = 0.25f;
     pa_plan_t *fallback = nullptr;    // next-wider plan (FP32 -> FP64 -> NTT64) for keys that fail the guard
+    RealMode *real = nullptr;         // half-length form for single keys (not in the exact mode)
     PendingBatch pending;             // a batch issued by pa_hash_batch_async, not yet finished
     cudaEvent_t done = nullptr;       // recorded behind the margins' (and host outputs') read-back
     // host batches (pa_hash_host_async): device staging rows and the copy streams around the compute
@@ -275,6 +287,19 @@ TwTab<T> tw_of(const pa_plan_t *p) {
     return t;
 }
 
+template <typename T>
+TwTab<T> tw_of_real(const RealMode *r) {
+    TwTab<T> t;
+    t.hi = static_cast<const cx<T> *>(r->tw_hi);
+    t.lo = static_cast<const cx<T> *>(r->tw_lo);
+    t.B = r->twB;
+    t.lgL = 0;
+    while ((1ull << t.lgL) < r->geo.L) ++t.lgL;
+    t.fine = static_cast<const cx<T> *>(r->tw_fine);
+    t.F = r->geo.F();
+    return t;
+}
+
 int ensure_work(pa_plan_t *p, uint32_t pairs) {
     if (pairs <= p->work_pairs) return PA_OK;
     if (p->work) {
@@ -347,9 +372,46 @@ int run_seed(pa_plan_t *p, const uint64_t *seed, cudaStream_t st) {
     return PA_OK;
 }
 
+// Seed tables of the half-length form: packed seed transform, then the bin-pair split.
+template <typename T>
+int run_seed_real(pa_plan_t *p, const uint64_t *seed, cudaStream_t st) {
+    RealMode *r = p->real;
+    const TwTab<T> tw = tw_of_real<T>(r);
+    cx<T> *W = static_cast<cx<T> *>(p->work);
+    const Geometry &g = r->geo;
+    const uint64_t N = g.L;
+    PA_CUDA(launch_fwd_seed<T>(g.lg1, seed, p->n, p->m, W, N, tw, st, true));
+    if (g.lgM) PA_CUDA(launch_mid<T>(g.lgM, false, W, N, g.inner(), 1, tw, st));
+    PA_CUDA(launch_middle_real<T>(g.ro, g.lgI, 1, W, static_cast<cx<T> *>(r->tabs), N, (uint32_t)g.lg1,
+                                  (uint32_t)g.lgM, tw, (T)(1.0 / (double)N), 1, st));
+    return PA_OK;
+}
+
+// One key through the half-length form.
+template <typename T>
+int run_key_real(pa_plan_t *p, const uint64_t *key, uint64_t kstride, uint64_t *out, uint64_t ostride,
+                 uint32_t *popc, uint32_t *marg, cudaStream_t st) {
+    RealMode *r = p->real;
+    const TwTab<T> tw = tw_of_real<T>(r);
+    cx<T> *W = static_cast<cx<T> *>(p->work);
+    const Geometry &g = r->geo;
+    const uint64_t N = g.L;
+    { Timed t_(p, K_PREP, st); PA_CUDA(launch_zero_keys(1, popc, marg, st)); }
+    { Timed t_(p, K_FWD_KEYS, st); PA_CUDA(launch_fwd_keys<T>(g.lg1, key, 1, kstride, p->n, W, N, 1, tw, popc, st, p->koff, true)); }
+    if (g.lgM) { Timed t_(p, K_MID_FWD, st); PA_CUDA(launch_mid<T>(g.lgM, false, W, N, g.inner(), 1, tw, st)); }
+    { Timed t_(p, K_MIDDLE_CONV, st); PA_CUDA(launch_middle_real<T>(g.ro, g.lgI, 0, W, static_cast<cx<T> *>(r->tabs), N, (uint32_t)g.lg1, (uint32_t)g.lgM, tw, (T)1, 1, st)); }
+    if (g.lgM) { Timed t_(p, K_MID_INV, st); PA_CUDA(launch_mid<T>(g.lgM, true, W, N, g.inner(), 1, tw, st)); }
+    { Timed t_(p, K_INV_BITS, st); PA_CUDA(launch_inv_bits<T>(g.lg1, W, N, p->m, 1, popc, marg, out, ostride, 1, tw, st, p->modified ? key : nullptr, kstride, true)); }
+    return PA_OK;
+}
+
 template <typename T>
 int run_keys(pa_plan_t *p, const uint64_t *keys, uint32_t nkeys, uint64_t kstride, uint64_t *out,
              uint64_t ostride, uint32_t *popc, uint32_t *marg, cudaStream_t st) {
+    if constexpr (!std::is_same<T, Zp>::value) {
+        if (nkeys == 1 && p->real && p->real->seeded)
+            return run_key_real<T>(p, keys, kstride, out, ostride, popc, marg, st);
+    }
     const TwTab<T> tw = tw_of<T>(p);
     cx<T> *W = static_cast<cx<T> *>(p->work);
     cx<T> *spec = static_cast<cx<T> *>(p->spec);
@@ -390,6 +452,13 @@ void free_plan(pa_plan_t *p) {
     cudaFree(p->seed_copy);
     if (p->h_marg) cudaFreeHost(p->h_marg);
     if (p->done) cudaEventDestroy(p->done);
+    if (p->real) {
+        cudaFree(p->real->tw_hi);
+        cudaFree(p->real->tw_lo);
+        cudaFree(p->real->tw_fine);
+        cudaFree(p->real->tabs);
+        delete p->real;
+    }
     cudaFree(p->stage_keys);
     cudaFree(p->stage_out);
     if (p->ev_in) cudaEventDestroy(p->ev_in);
@@ -537,6 +606,28 @@ int tune_split(pa_plan_t *p, const std::vector<Geometry> &cand) {
     return fail(PA_OK);
 }
 
+// The half-length form of a plan: the smallest supported N with 2N >= n+m-1 whose
+// innermost pass fits the two-row kernel; left out (nullptr) if there is none.
+int build_real_mode(pa_plan_t *p) {
+    const uint64_t need = p->n + p->m - 1;
+    const Geometry g = choose_geometry((need + 1) / 2, p->dtype, true);
+    if (g.L == 0) return PA_OK;
+    RealMode *r = new RealMode();
+    r->geo = g;
+    int rc = pa_internal_twiddles(g.L, g.F(), (int)p->dtype, &r->tw_hi, &r->tw_lo, &r->twB, &r->tw_fine);
+    if (rc == PA_OK) {
+        cudaError_t e = cudaMalloc(&r->tabs, (size_t)3 * g.L * elem_bytes(p->dtype));
+        if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();
+            rc = PA_ENOMEM;
+        } else if (e != cudaSuccess) {
+            rc = cuda_fail(e, "cudaMalloc(real tables)");
+        }
+    }
+    p->real = r;  // released with the plan, also on failure
+    return rc;
+}
+
 // pa_plan (or pa_plan_modified), with the split forced when `force` is given. For the
 // modified hash, n is the key length and the Toeplitz block is m x (n - m).
 int plan_create(uint64_t n, uint64_t m, pa_dtype_t dtype, const Geometry *force, pa_plan_t **out,
@@ -580,6 +671,7 @@ int plan_create(uint64_t n, uint64_t m, pa_dtype_t dtype, const Geometry *force,
         if (cand.size() > 1) rc = tune_split(p, cand);
     }
     if (rc == PA_OK) rc = build_plan_twiddles(p);
+    if (rc == PA_OK && dtype != PA_NTT64) rc = build_real_mode(p);
     if (rc != PA_OK) {
         free_plan(p);
         return rc;
@@ -819,6 +911,13 @@ int pa_set_seed(pa_plan_t *p, const uint64_t *seed_dev, uint64_t seed_bits, pa_s
          : (p->dtype == PA_FP64)     ? run_seed<double>(p, p->seed_copy, st)
                                      : run_seed<Zp>(p, p->seed_copy, st);
     if (rc != PA_OK) return rc;
+    if (p->real) {
+        p->real->seeded = false;
+        rc = (p->dtype == PA_FP32_GUARD) ? run_seed_real<float>(p, p->seed_copy, st)
+                                         : run_seed_real<double>(p, p->seed_copy, st);
+        if (rc != PA_OK) return rc;
+        p->real->seeded = true;
+    }
     p->seeded = true;
     if (p->fallback) p->fallback->seeded = false;  // re-seeded lazily on the next escalation
     return PA_OK;

@@ -70,18 +70,23 @@ template <typename T> struct Enc {
     static __device__ __forceinline__ E seed(bool in_range, uint32_t bit) {
         return Arith<T>::mk(in_range ? (bit ? (T)-1 : (T)1) : (T)0, (T)0);
     }
-    // bits and margins of the two keys carried by v
+    static __device__ __forceinline__ E seed_pair(bool in0, uint32_t b0, bool in1, uint32_t b1) {
+        return Arith<T>::mk(in0 ? (b0 ? (T)-1 : (T)1) : (T)0, in1 ? (b1 ? (T)-1 : (T)1) : (T)0);
+    }
+    // bits and margins of the two values carried by v (valid_b: the imaginary part's own range)
     static __device__ __forceinline__ void decode(E v, uint32_t popa, uint32_t popb, bool valid, bool &bit_a,
                                                   bool &bit_b, M &ma, M &mb) {
+        decode2(v, popa, popb, valid, valid, bit_a, bit_b, ma, mb);
+    }
+    static __device__ __forceinline__ void decode2(E v, uint32_t popa, uint32_t popb, bool valid_a, bool valid_b,
+                                                   bool &bit_a, bool &bit_b, M &ma, M &mb) {
         const T wa = ((T)(popa & 3u) - v.x) * (T)0.5, wb = ((T)(popb & 3u) - v.y) * (T)0.5;
         const T fa = wa + Magic<T>::v, fb = wb + Magic<T>::v;  // rint via the 1.5*2^p addition
-        bit_a = valid && low_bit(fa);
-        bit_b = valid && low_bit(fb);
-        if (valid) {
-            // beyond the limit the parity is not resolvable: report a margin of 1 so the guard escalates
-            ma = fmax(ma, fabs(wa) < Magic<T>::limit ? fabs(wa - (fa - Magic<T>::v)) : (T)1);
-            mb = fmax(mb, fabs(wb) < Magic<T>::limit ? fabs(wb - (fb - Magic<T>::v)) : (T)1);
-        }
+        bit_a = valid_a && low_bit(fa);
+        bit_b = valid_b && low_bit(fb);
+        // beyond the limit the parity is not resolvable: report a margin of 1 so the guard escalates
+        if (valid_a) ma = fmax(ma, fabs(wa) < Magic<T>::limit ? fabs(wa - (fa - Magic<T>::v)) : (T)1);
+        if (valid_b) mb = fmax(mb, fabs(wb) < Magic<T>::limit ? fabs(wb - (fb - Magic<T>::v)) : (T)1);
     }
 };
 template <> struct Enc<Zp> {
@@ -89,10 +94,17 @@ template <> struct Enc<Zp> {
     using M = float;
     static __device__ __forceinline__ E key_pair(uint32_t ba, uint32_t bb) { return (E)ba | ((E)bb << 32); }
     static __device__ __forceinline__ E seed(bool in_range, uint32_t bit) { return (in_range && bit) ? 1ull : 0ull; }
+    // (the exact transform has no half-length packing of one key: its values are not complex)
+    static __device__ __forceinline__ E seed_pair(bool, uint32_t, bool, uint32_t) { return 0ull; }
     static __device__ __forceinline__ void decode(E v, uint32_t, uint32_t, bool valid, bool &bit_a, bool &bit_b, M &,
                                                   M &) {
         bit_a = valid && (v & 1ull);
         bit_b = valid && ((v >> 32) & 1ull);
+    }
+    static __device__ __forceinline__ void decode2(E v, uint32_t, uint32_t, bool valid_a, bool valid_b, bool &bit_a,
+                                                   bool &bit_b, M &, M &) {
+        bit_a = valid_a && (v & 1ull);
+        bit_b = valid_b && ((v >> 32) & 1ull);
     }
 };
 
@@ -106,6 +118,24 @@ __device__ __forceinline__ uint32_t *key_stage(unsigned char *smem_raw) {
 }
 template <typename T, int LEN, int COLS>
 constexpr size_t stage_bytes() { return (size_t)LEN * sizeof(uint32_t); }
+
+// Single keys in half-length transforms: transform element t carries key bits 2t
+// (real part) and 2t+1 (imaginary part). even_bits gathers the even-position bits of
+// x into the low 16 bits; spread_bits is its inverse (low 16 bits to even positions).
+__device__ __forceinline__ uint32_t even_bits(uint32_t x) {
+    x &= 0x55555555u;
+    x = (x | (x >> 1)) & 0x33333333u;
+    x = (x | (x >> 2)) & 0x0F0F0F0Fu;
+    x = (x | (x >> 4)) & 0x00FF00FFu;
+    return (x | (x >> 8)) & 0x0000FFFFu;
+}
+__device__ __forceinline__ uint32_t spread_bits(uint32_t x) {
+    x &= 0x0000FFFFu;
+    x = (x | (x << 8)) & 0x00FF00FFu;
+    x = (x | (x << 4)) & 0x0F0F0F0Fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    return (x | (x << 1)) & 0x55555555u;
+}
 
 // COLS bits of v starting at bit t0 (t0 % COLS == 0, so they sit in one word);
 // bits at or past nbits read as 0.
@@ -134,7 +164,9 @@ __device__ __forceinline__ uint32_t bits_at(const uint64_t *v, uint64_t nbits, u
 // ---------------------------------------------------------------------------
 // Level-1 forward pass from packed key bits. Grid (S/COLS, pairs); pair p
 // carries key 2p in the real part and key 2p+1 (if any) in the imaginary part.
-template <typename T, int LEN, int COLS, int E>
+// PACK: slot p carries one key, p, in a half-length transform: element t is key
+// bits 2t (real part) and 2t+1 (imaginary part).
+template <typename T, int LEN, int COLS, int E, bool PACK = false>
 __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
     k_fwd_keys(const uint64_t *__restrict__ keys, uint32_t nkeys, uint64_t kstride, uint64_t n,
                cx<T> *__restrict__ W, uint64_t L, TwTab<T> tw, uint32_t *__restrict__ popc, uint64_t koff) {
@@ -154,11 +186,15 @@ __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
     // Toeplitz hash, whose Toeplitz block multiplies key bits m .. n-1).
     const uint64_t nk = n + koff;
     const bool aligned = (koff % COLS) == 0;
-    const uint64_t *xa = keys + (uint64_t)(2 * pair) * kstride, *xb = xa + kstride;
+    const uint64_t *xa = keys + (uint64_t)(PACK ? pair : 2 * pair) * kstride, *xb = xa + kstride;
     for (uint32_t a = threadIdx.x; a < LEN; a += blockDim.x) {
         const uint64_t t0 = (uint64_t)a * S + u0 + koff;  // S % 64 == 0: aligned COLS bits sit in one word
         uint32_t wa, wb = 0u;
-        if (aligned) {
+        if constexpr (PACK) {  // 2*COLS key bits from 2*(a*S + u0): the even ones real, the odd ones imaginary
+            const uint32_t c = bits_at(xa, nk, 2 * ((uint64_t)a * S + u0) + koff, 2 * COLS);
+            wa = even_bits(c);
+            wb = even_bits(c >> 1);
+        } else if (aligned) {
             wa = aligned_bits<COLS>(xa, nk, t0);
             if (has_b) wb = aligned_bits<COLS>(xb, nk, t0);
         } else {
@@ -172,8 +208,12 @@ __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
     ca = __reduce_add_sync(0xffffffffu, ca);
     cb = __reduce_add_sync(0xffffffffu, cb);
     if ((threadIdx.x & 31) == 0 && (ca | cb)) {
-        if (ca) atomicAdd(popc + 2 * pair, ca);
-        if (cb) atomicAdd(popc + 2 * pair + 1, cb);
+        if (PACK) {
+            atomicAdd(popc + pair, ca + cb);
+        } else {
+            if (ca) atomicAdd(popc + 2 * pair, ca);
+            if (cb) atomicAdd(popc + 2 * pair + 1, cb);
+        }
     }
     __syncthreads();
     cx<T> v[E];
@@ -190,8 +230,10 @@ __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
     for (int s = 0; s < E; ++s) w[(uint64_t)idx_e<LEN, E>(tq, s) * S + u] = v[s];
 }
 
-// Level-1 forward pass of the rotated, +-1 encoded seed (real input).
-template <typename T, int LEN, int COLS, int E>
+// Level-1 forward pass of the rotated, +-1 encoded seed (real input). PACK: the
+// seed of a length-2L convolution in a length-L transform, element t carrying
+// rotated positions 2t (real part) and 2t+1 (imaginary part).
+template <typename T, int LEN, int COLS, int E, bool PACK = false>
 __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
     k_fwd_seed(const uint64_t *__restrict__ seed, uint64_t n, uint64_t m, cx<T> *__restrict__ W, uint64_t L,
                TwTab<T> tw) {
@@ -205,11 +247,25 @@ __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
 #pragma unroll
     for (int s = 0; s < E; ++s) {
         const uint64_t pos = (uint64_t)idx_r0<LEN, E>(tq, s) * S + u;
-        uint64_t j = pos + n - 1;  // seed index whose value sits at rotated position pos
-        if (j >= L) j -= L;
-        const bool in_range = j < sbits;
-        const uint32_t bit = in_range ? (uint32_t)(__ldg(seed + (j >> 6)) >> (j & 63)) & 1u : 0u;
-        v[s] = Enc<T>::seed(in_range, bit);
+        if constexpr (PACK) {
+            const uint64_t L2 = 2 * L;
+            uint32_t bit[2];
+            bool in_range[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                uint64_t j = 2 * pos + h + n - 1;  // seed index at rotated position 2*pos + h
+                if (j >= L2) j -= L2;
+                in_range[h] = j < sbits;
+                bit[h] = in_range[h] ? (uint32_t)(__ldg(seed + (j >> 6)) >> (j & 63)) & 1u : 0u;
+            }
+            v[s] = Enc<T>::seed_pair(in_range[0], bit[0], in_range[1], bit[1]);
+        } else {
+            uint64_t j = pos + n - 1;  // seed index whose value sits at rotated position pos
+            if (j >= L) j -= L;
+            const bool in_range = j < sbits;
+            const uint32_t bit = in_range ? (uint32_t)(__ldg(seed + (j >> 6)) >> (j & 63)) & 1u : 0u;
+            v[s] = Enc<T>::seed(in_range, bit);
+        }
     }
     cta_fft<T, LEN, COLS, E, false>(sm, v, tq, col, tw);
     twiddle_chain<T, false, E>(v, tw, (uint32_t)(tq * u), (uint32_t)((LEN / E) * u));
@@ -402,7 +458,9 @@ __device__ __forceinline__ float margin_to_float(double x) { return __double2flo
 // Output bit i = element i of the convolution window; bits >= m are written 0.
 // Each key's rounding margin max |w - rint(w)| goes to margin_bits (float bits,
 // atomicMax; all margins are >= 0 so integer order equals float order).
-template <typename T, int LEN, int COLS, int E>
+// PACK: slot p holds one key p of a half-length transform; element t carries output
+// bits 2t (real part) and 2t+1 (imaginary part).
+template <typename T, int LEN, int COLS, int E, bool PACK = false>
 __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
     k_inv_bits(const cx<T> *__restrict__ W, uint64_t L, uint64_t m, uint32_t nkeys,
                const uint32_t *__restrict__ popc, uint32_t *__restrict__ margin_bits, uint64_t *__restrict__ out,
@@ -416,8 +474,8 @@ __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
     const uint64_t u0 = (uint64_t)blockIdx.x * COLS;
     const uint64_t u = u0 + col;
     const uint32_t pair = blockIdx.y;
-    const uint32_t ka = 2 * pair, kb = 2 * pair + 1;
-    const bool has_b = kb < nkeys;
+    const uint32_t ka = PACK ? pair : 2 * pair, kb = 2 * pair + 1;
+    const bool has_b = !PACK && kb < nkeys;
     const cx<T> *w = W + (uint64_t)pair * L;
     cx<T> v[E];
 #pragma unroll
@@ -426,11 +484,38 @@ __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
     cta_fft<T, LEN, COLS, E, true>(sm, v, tq, col, tw);
 
     const uint32_t popa = popc[ka];
-    const uint32_t popb = has_b ? popc[kb] : 0u;
+    const uint32_t popb = PACK ? popa : (has_b ? popc[kb] : 0u);
     word_t *oa = reinterpret_cast<word_t *>(out + (uint64_t)ka * ostride);
     word_t *ob = reinterpret_cast<word_t *>(out + (uint64_t)kb * ostride);
     const uint64_t nchunks = ((m + 63) >> 6) * (64 / COLS);
     typename Enc<T>::M ma = 0, mb = 0;
+    if constexpr (PACK) {
+        // chunk ci: the row's COLS elements t = t1*S + u0 + c, i.e. output bits 2*(t1*S + u0) .. +2*COLS
+        using word2_t = typename BitsWord<2 * COLS>::type;
+        word2_t *o2 = reinterpret_cast<word2_t *>(out + (uint64_t)ka * ostride);
+        const uint64_t nchunks2 = ((m + 63) >> 6) * (64 / (2 * COLS));
+#pragma unroll
+        for (int s = 0; s < E; ++s) {
+            const uint64_t t1 = idx_r0<LEN, E>(tq, s);
+            const uint64_t t = t1 * S + u;
+            const uint64_t ci = (t1 * S + u0) / COLS;
+            if (!__any_sync(0xffffffffu, ci < nchunks2)) continue;
+            bool bit_e, bit_o;
+            Enc<T>::decode2(v[s], popa, popa, 2 * t < m, 2 * t + 1 < m, bit_e, bit_o, ma, mb);
+            const uint32_t be = __ballot_sync(0xffffffffu, bit_e);
+            const uint32_t bo = __ballot_sync(0xffffffffu, bit_o);
+            if (col == 0 && ci < nchunks2) {
+                const uint32_t msk = (1u << COLS) - 1u;
+                uint32_t y = spread_bits((be >> lane) & msk) | (spread_bits((bo >> lane) & msk) << 1);
+                if (xkeys) y ^= bits_at(xkeys + (uint64_t)ka * xstride, m, 2 * (t1 * S + u0), 2 * COLS);
+                o2[ci] = (word2_t)y;
+            }
+        }
+        uint32_t f = __float_as_uint(margin_to_float(ma > mb ? ma : mb));
+        f = __reduce_max_sync(0xffffffffu, f);
+        if (lane == 0) atomicMax(margin_bits + ka, f);
+        return;
+    }
 #pragma unroll
     for (int s = 0; s < E; ++s) {
         const uint64_t t1 = idx_r0<LEN, E>(tq, s);
@@ -619,6 +704,91 @@ __global__ void __launch_bounds__(2 * (LEN / E), min_blocks_inner(2 * (LEN / E))
         cta_fft_inv_odd<T, LEN, E>(sm, y, tq, tw, [&](uint32_t i, cx<T> x) {
             if (store) wo[i] = x;
         });
+    }
+}
+
+// Fused innermost pass of a single key in a half-length transform (the real-input
+// form of the convolution theorem; paper Eq. 5-10 give the same split for a key and
+// a seed). The slot holds Z = FFT_N(z), z[t] = x[2t] + i x[2t+1], N = L/2. With the
+// mirror bin Z' = Z[N-k]: E_x = (Z + conj Z')/2 and O_x = (Z - conj Z')/(2i) are the
+// spectra of the even and odd key bits, and with the seed tables (per bin, times 1/N)
+// Es = E_s, Os = O_s and Bp = w_N^k O_s of the seed's even/odd spectra, the product
+// Y = S X of the length-L transforms is, in even/odd form,
+//     E_y = Es E_x + Bp O_x,   O_y = Es O_x + Os E_x,
+// and the inverse transform of E_y + i O_y returns y[2t] + i y[2t+1].
+// CTA (rho, slot): rows rho and -rho (one thread group each), as in k_middle_split.
+// MODE 1 builds the tables from the seed slot instead (forward transform and split only).
+template <typename T, int LEN, int E, int MODE>
+__global__ void __launch_bounds__(2 * (LEN / E), min_blocks_inner(2 * (LEN / E)))
+    k_middle_real(cx<T> *__restrict__ W, cx<T> *__restrict__ tabs, uint64_t N, uint32_t lgL1, uint32_t lgM,
+                  TwTab<T> tw, T scale) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T> *smem = reinterpret_cast<cx<T> *>(smem_raw);
+    constexpr uint32_t TC = LEN / E;
+    constexpr uint32_t SE = smem_elems<LEN, 1>();
+    const uint32_t g = threadIdx.x / TC, tq = threadIdx.x % TC;
+    const uint32_t R = (uint32_t)(N / LEN);  // rows
+    const uint32_t rho = blockIdx.x;          // 0 .. R/2
+    const uint32_t rho_m = (R - rho) & (R - 1);
+    const uint32_t my_rho = g ? rho_m : rho;
+    const uint32_t row = split_row(my_rho, lgL1, lgM);
+    const bool self_paired = rho == rho_m;
+    cx<T> *sm = smem + g * SE;
+    const cx<T> *sm_other = smem + (self_paired ? g : 1u - g) * SE;
+    cx<T> *w = W + (uint64_t)blockIdx.y * N + (uint64_t)row * LEN;
+    cx<T> v[E];
+    if constexpr (Plan<LEN, E>::RO == 1) {
+#pragma unroll
+        for (int s = 0; s < E; ++s) v[s] = w[idx_r0<LEN, E>(tq, s)];
+        cta_fft<T, LEN, 1, E, false>(sm, v, tq, 0, tw);
+    } else {
+        cta_fft_fwd_odd<T, LEN, E>(sm, v, tq, tw, [&](uint32_t i) { return w[i]; });
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < E; ++s) sm[sidx<1>(idx_e<LEN, E>(tq, s), 0)] = v[s];
+    __syncthreads();
+    const cx<T> *Es = tabs, *Os = tabs + N, *Bp = tabs + 2 * N;
+    const bool write_tab = !(self_paired && g == 1);
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+        const uint32_t p = idx_e<LEN, E>(tq, s);
+        // mirror of position p: -p mod LEN in the row of the zero frequency low part, else LEN-1-p
+        const uint32_t pm = (my_rho == 0) ? (p == 0 ? 0u : (uint32_t)LEN - p) : ((uint32_t)LEN - 1u - p);
+        const cx<T> z = v[s], zm = sm_other[sidx<1>(pm, 0)];
+        const cx<T> ex = Arith<T>::mk((z.x + zm.x) * (T)0.5, (z.y - zm.y) * (T)0.5);
+        const cx<T> ox = Arith<T>::mk((z.y + zm.y) * (T)0.5, (zm.x - z.x) * (T)0.5);
+        const uint64_t e = (uint64_t)row * LEN + p;
+        if constexpr (MODE == 1) {
+            if (write_tab) {
+                const cx<T> es = Arith<T>::mk(ex.x * scale, ex.y * scale);
+                const cx<T> os = Arith<T>::mk(ox.x * scale, ox.y * scale);
+                // frequency of this bin: low part from the strided passes, high part p
+                const uint32_t k = my_rho + R * p;
+                tabs[e] = es;
+                tabs[N + e] = os;
+                tabs[2 * N + e] = Arith<T>::mul(Arith<T>::template omega<false>(tw, k), os);
+            }
+        } else {
+            const cx<T> es = Es[e], os = Os[e], bp = Bp[e];
+            const cx<T> ey = Arith<T>::add(Arith<T>::mul(es, ex), Arith<T>::mul(bp, ox));
+            const cx<T> oy = Arith<T>::add(Arith<T>::mul(es, ox), Arith<T>::mul(os, ex));
+            v[s] = Arith<T>::mk(ey.x - oy.y, ey.y + oy.x);  // E_y + i O_y
+        }
+    }
+    if constexpr (MODE == 0) {
+        __syncthreads();  // the mirror reads of both groups are done
+        const bool store = !(self_paired && g == 1);  // a self-paired row is written once
+        if constexpr (Plan<LEN, E>::RO == 1) {
+            cta_fft<T, LEN, 1, E, true>(sm, v, tq, 0, tw);
+            if (!store) return;
+#pragma unroll
+            for (int s = 0; s < E; ++s) w[idx_r0<LEN, E>(tq, s)] = v[s];
+        } else {
+            cta_fft_inv_odd<T, LEN, E>(sm, v, tq, tw, [&](uint32_t i, cx<T> x) {
+                if (store) w[i] = x;
+            });
+        }
     }
 }
 

@@ -42,36 +42,58 @@ static cudaError_t by_len(int lg, F &&f) {
     }
 }
 
+template <typename T, int LEN, bool PACK>
+cudaError_t fwd_keys_at(const uint64_t *keys, uint32_t nkeys, uint64_t kstride, uint64_t n, cx<T> *W, uint64_t L,
+                        uint32_t pairs, TwTab<T> tw, uint32_t *popc, cudaStream_t st, uint64_t koff) {
+    constexpr int E = Shape<T>::E, COLS = Shape<T>::COLS;
+    auto kern = k_fwd_keys<T, LEN, COLS, E, PACK>;
+    constexpr size_t sb = smem_bytes<T, LEN, COLS>() + stage_bytes<T, LEN, COLS>();
+    cudaError_t e = set_smem(kern, sb);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((L / LEN) / COLS), pairs);
+    kern<<<grid, COLS * LEN / E, sb, st>>>(keys, nkeys, kstride, n, W, L, tw, popc, koff);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_fwd_keys(int lgLEN, const uint64_t *keys, uint32_t nkeys, uint64_t kstride, uint64_t n,
                             cx<T> *W, uint64_t L, uint32_t pairs, TwTab<T> tw, uint32_t *popc, cudaStream_t st,
-                            uint64_t koff) {
-    constexpr int E = Shape<T>::E, COLS = Shape<T>::COLS;
+                            uint64_t koff, bool pack) {
     return by_len<kMinLgStrided, kMaxLgStrided>(lgLEN, [&](auto c) {
         constexpr int LEN = decltype(c)::value;
-        auto kern = k_fwd_keys<T, LEN, COLS, E>;
-        constexpr size_t sb = smem_bytes<T, LEN, COLS>() + stage_bytes<T, LEN, COLS>();
-        cudaError_t e = set_smem(kern, sb);
-        if (e != cudaSuccess) return e;
-        dim3 grid((unsigned)((L / LEN) / COLS), pairs);
-        kern<<<grid, COLS * LEN / E, sb, st>>>(keys, nkeys, kstride, n, W, L, tw, popc, koff);
-        return cudaGetLastError();
+        if constexpr (!std::is_same<T, Zp>::value) {
+            if (pack) return fwd_keys_at<T, LEN, true>(keys, nkeys, kstride, n, W, L, pairs, tw, popc, st, koff);
+        } else {
+            if (pack) return cudaErrorInvalidValue;  // the exact transform has no half-length packing
+        }
+        return fwd_keys_at<T, LEN, false>(keys, nkeys, kstride, n, W, L, pairs, tw, popc, st, koff);
     });
+}
+
+template <typename T, int LEN, bool PACK>
+cudaError_t fwd_seed_at(const uint64_t *seed, uint64_t n, uint64_t m, cx<T> *W, uint64_t L, TwTab<T> tw,
+                        cudaStream_t st) {
+    constexpr int E = Shape<T>::E, COLS = Shape<T>::COLS;
+    auto kern = k_fwd_seed<T, LEN, COLS, E, PACK>;
+    constexpr size_t sb = smem_bytes<T, LEN, COLS>();
+    cudaError_t e = set_smem(kern, sb);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((L / LEN) / COLS), 1);
+    kern<<<grid, COLS * LEN / E, sb, st>>>(seed, n, m, W, L, tw);
+    return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_fwd_seed(int lgLEN, const uint64_t *seed, uint64_t n, uint64_t m, cx<T> *W, uint64_t L,
-                            TwTab<T> tw, cudaStream_t st) {
-    constexpr int E = Shape<T>::E, COLS = Shape<T>::COLS;
+                            TwTab<T> tw, cudaStream_t st, bool pack) {
     return by_len<kMinLgStrided, kMaxLgStrided>(lgLEN, [&](auto c) {
         constexpr int LEN = decltype(c)::value;
-        auto kern = k_fwd_seed<T, LEN, COLS, E>;
-        constexpr size_t sb = smem_bytes<T, LEN, COLS>();
-        cudaError_t e = set_smem(kern, sb);
-        if (e != cudaSuccess) return e;
-        dim3 grid((unsigned)((L / LEN) / COLS), 1);
-        kern<<<grid, COLS * LEN / E, sb, st>>>(seed, n, m, W, L, tw);
-        return cudaGetLastError();
+        if constexpr (!std::is_same<T, Zp>::value) {
+            if (pack) return fwd_seed_at<T, LEN, true>(seed, n, m, W, L, tw, st);
+        } else {
+            if (pack) return cudaErrorInvalidValue;
+        }
+        return fwd_seed_at<T, LEN, false>(seed, n, m, W, L, tw, st);
     });
 }
 
@@ -216,36 +238,52 @@ cudaError_t launch_middle_odd(int lg, int mode, cx<T> *W, cx<T> *spec, uint64_t 
     return odd_middle_dispatch<T, RO>(lg, mode, W, spec, L, pairs, tw, scale, st, err);
 }
 
+template <typename T, int LEN, bool PACK>
+cudaError_t inv_bits_at(const cx<T> *W, uint64_t L, uint64_t m, uint32_t nkeys, const uint32_t *popc,
+                        uint32_t *margin_bits, uint64_t *out, uint64_t ostride, uint32_t pairs, TwTab<T> tw,
+                        cudaStream_t st, const uint64_t *xkeys, uint64_t xstride) {
+    constexpr int E = Shape<T>::E, COLS = Shape<T>::COLS;
+    auto kern = k_inv_bits<T, LEN, COLS, E, PACK>;
+    constexpr size_t sb = smem_bytes<T, LEN, COLS>();
+    cudaError_t e = set_smem(kern, sb);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((L / LEN) / COLS), pairs);
+    kern<<<grid, COLS * LEN / E, sb, st>>>(W, L, m, nkeys, popc, margin_bits, out, ostride, tw, xkeys, xstride);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_inv_bits(int lgLEN, const cx<T> *W, uint64_t L, uint64_t m, uint32_t nkeys,
                             const uint32_t *popc, uint32_t *margin_bits, uint64_t *out, uint64_t ostride,
                             uint32_t pairs, TwTab<T> tw, cudaStream_t st, const uint64_t *xkeys,
-                            uint64_t xstride) {
-    constexpr int E = Shape<T>::E, COLS = Shape<T>::COLS;
+                            uint64_t xstride, bool pack) {
     return by_len<kMinLgStrided, kMaxLgStrided>(lgLEN, [&](auto c) {
         constexpr int LEN = decltype(c)::value;
-        auto kern = k_inv_bits<T, LEN, COLS, E>;
-        constexpr size_t sb = smem_bytes<T, LEN, COLS>();
-        cudaError_t e = set_smem(kern, sb);
-        if (e != cudaSuccess) return e;
-        dim3 grid((unsigned)((L / LEN) / COLS), pairs);
-        kern<<<grid, COLS * LEN / E, sb, st>>>(W, L, m, nkeys, popc, margin_bits, out, ostride, tw, xkeys, xstride);
-        return cudaGetLastError();
+        if constexpr (!std::is_same<T, Zp>::value) {
+            if (pack)
+                return inv_bits_at<T, LEN, true>(W, L, m, nkeys, popc, margin_bits, out, ostride, pairs, tw, st,
+                                                 xkeys, xstride);
+        } else {
+            if (pack) return cudaErrorInvalidValue;
+        }
+        return inv_bits_at<T, LEN, false>(W, L, m, nkeys, popc, margin_bits, out, ostride, pairs, tw, st, xkeys,
+                                          xstride);
     });
 }
 
 #define PA_INSTANTIATE_LAUNCHERS(T)                                                                              \
     template cudaError_t launch_fwd_keys<T>(int, const uint64_t *, uint32_t, uint64_t, uint64_t, cx<T> *,        \
-                                            uint64_t, uint32_t, TwTab<T>, uint32_t *, cudaStream_t, uint64_t);   \
+                                            uint64_t, uint32_t, TwTab<T>, uint32_t *, cudaStream_t, uint64_t,    \
+                                            bool);                                                               \
     template cudaError_t launch_fwd_seed<T>(int, const uint64_t *, uint64_t, uint64_t, cx<T> *, uint64_t,        \
-                                            TwTab<T>, cudaStream_t);                                             \
+                                            TwTab<T>, cudaStream_t, bool);                                       \
     template cudaError_t launch_mid<T>(int, bool, cx<T> *, uint64_t, uint32_t, uint32_t, TwTab<T>,               \
                                        cudaStream_t);                                                           \
     template cudaError_t launch_middle<T>(int, int, int, cx<T> *, cx<T> *, uint64_t, uint32_t, TwTab<T>, cx<T>,  \
                                           cudaStream_t, uint32_t *);                                            \
     template cudaError_t launch_inv_bits<T>(int, const cx<T> *, uint64_t, uint64_t, uint32_t, const uint32_t *,  \
                                             uint32_t *, uint64_t *, uint64_t, uint32_t, TwTab<T>, cudaStream_t,  \
-                                            const uint64_t *, uint64_t);
+                                            const uint64_t *, uint64_t, bool);
 
 template <typename T>
 cudaError_t launch_fwd_keyseed(int lgLEN, const BlockDev *blocks, uint32_t nblocks, cx<T> *W, uint64_t L,
@@ -336,13 +374,76 @@ cudaError_t launch_inv_bits_blocks(int lgLEN, const cx<T> *Wi, uint64_t L, const
     template cudaError_t launch_middle_split<T>(int, int, const cx<T> *, cx<T> *, uint64_t, uint32_t, uint32_t,  \
                                                 uint32_t, TwTab<T>, cudaStream_t);                               \
     template cudaError_t launch_inv_bits_blocks<T>(int, const cx<T> *, uint64_t, const BlockDev *, uint32_t,     \
-                                                   const uint32_t *, uint32_t *, TwTab<T>, cudaStream_t);
+                                                   const uint32_t *, uint32_t *, TwTab<T>, cudaStream_t);        \
+    template cudaError_t launch_middle_real<T>(int, int, int, cx<T> *, cx<T> *, uint64_t, uint32_t, uint32_t,    \
+                                               TwTab<T>, T, uint32_t, cudaStream_t);
+
+// Single-key half-length innermost pass (k_middle_real): same lengths as the split pass.
+template <typename T, int LEN>
+cudaError_t real_at(int mode, cx<T> *W, cx<T> *tabs, uint64_t N, uint32_t lgL1, uint32_t lgM, TwTab<T> tw, T scale,
+                    uint32_t slots, cudaStream_t st) {
+    constexpr int E = Shape<T>::E;
+    constexpr size_t sb = 2 * smem_bytes<T, LEN, 1>();
+    const uint32_t R = (uint32_t)(N / LEN);
+    dim3 grid(R / 2 + 1, slots);
+    if (mode == 0) {
+        auto kern = k_middle_real<T, LEN, E, 0>;
+        cudaError_t e = set_smem(kern, sb);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, 2 * (LEN / E), sb, st>>>(W, tabs, N, lgL1, lgM, tw, scale);
+    } else {
+        auto kern = k_middle_real<T, LEN, E, 1>;
+        cudaError_t e = set_smem(kern, sb);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, 2 * (LEN / E), sb, st>>>(W, tabs, N, lgL1, lgM, tw, scale);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T, int RO, int LG = kMinLgOdd>
+cudaError_t real_odd_dispatch(int lg, int mode, cx<T> *W, cx<T> *tabs, uint64_t N, uint32_t lgL1, uint32_t lgM,
+                              TwTab<T> tw, T scale, uint32_t slots, cudaStream_t st) {
+    if constexpr (LG > kMaxLgOdd) {
+        return cudaErrorInvalidValue;
+    } else {
+        if (lg == LG) {
+            if constexpr (odd_inner_ok<T>(RO, LG, true)) {
+                return real_at<T, RO * (1 << LG)>(mode, W, tabs, N, lgL1, lgM, tw, scale, slots, st);
+            } else {
+                return cudaErrorInvalidValue;
+            }
+        }
+        return real_odd_dispatch<T, RO, LG + 1>(lg, mode, W, tabs, N, lgL1, lgM, tw, scale, slots, st);
+    }
+}
+
+template <typename T, int RO>
+cudaError_t launch_middle_real_odd(int lg, int mode, cx<T> *W, cx<T> *tabs, uint64_t N, uint32_t lgL1, uint32_t lgM,
+                                   TwTab<T> tw, T scale, uint32_t slots, cudaStream_t st) {
+    return real_odd_dispatch<T, RO>(lg, mode, W, tabs, N, lgL1, lgM, tw, scale, slots, st);
+}
+
+template <typename T>
+cudaError_t launch_middle_real(int ro, int lg, int mode, cx<T> *W, cx<T> *tabs, uint64_t N, uint32_t lgL1,
+                               uint32_t lgM, TwTab<T> tw, T scale, uint32_t slots, cudaStream_t st) {
+    if (ro == 1) {
+        return by_len<kMinLgMiddle, MaxLgSplit<T>::v>(lg, [&](auto c) {
+            return real_at<T, decltype(c)::value>(mode, W, tabs, N, lgL1, lgM, tw, scale, slots, st);
+        });
+    }
+    if (ro == 3) return launch_middle_real_odd<T, 3>(lg, mode, W, tabs, N, lgL1, lgM, tw, scale, slots, st);
+    if (ro == 5) return launch_middle_real_odd<T, 5>(lg, mode, W, tabs, N, lgL1, lgM, tw, scale, slots, st);
+    if (ro == 9) return launch_middle_real_odd<T, 9>(lg, mode, W, tabs, N, lgL1, lgM, tw, scale, slots, st);
+    return cudaErrorInvalidValue;
+}
 
 // Odd innermost lengths of one (type, RO): the plain middle pass and the split pass.
 #define PA_INSTANTIATE_ODD(T, RO)                                                                               \
     template cudaError_t launch_middle_odd<T, RO>(int, int, cx<T> *, cx<T> *, uint64_t, uint32_t, TwTab<T>,     \
                                                   cx<T>, cudaStream_t, uint32_t *);                             \
     template cudaError_t launch_middle_split_odd<T, RO>(int, const cx<T> *, cx<T> *, uint64_t, uint32_t,        \
-                                                        uint32_t, uint32_t, TwTab<T>, cudaStream_t);
+                                                        uint32_t, uint32_t, TwTab<T>, cudaStream_t);            \
+    template cudaError_t launch_middle_real_odd<T, RO>(int, int, cx<T> *, cx<T> *, uint64_t, uint32_t, uint32_t, \
+                                                       TwTab<T>, T, uint32_t, cudaStream_t);
 
 }  // namespace pa

@@ -37,13 +37,15 @@ cudaError_t launch_zero_keys(uint32_t nkeys, uint32_t *popc, uint32_t *margin_bi
 // Level-1 forward pass of key pairs; also adds each key's popcount into popc[k]
 // (which must be zero beforehand: launch_zero_keys). The transform input is key
 // bits koff .. koff+n-1 (koff = m for the modified Toeplitz hash).
+// pack: one key per slot in a half-length transform (element t = key bits 2t, 2t+1).
 template <typename T>
 cudaError_t launch_fwd_keys(int lgLEN, const uint64_t *keys, uint32_t nkeys, uint64_t kstride, uint64_t n,
                             cx<T> *W, uint64_t L, uint32_t pairs, TwTab<T> tw, uint32_t *popc, cudaStream_t st,
-                            uint64_t koff = 0);
+                            uint64_t koff = 0, bool pack = false);
+// pack: the seed of a length-2L convolution in a length-L transform (positions 2t, 2t+1).
 template <typename T>
 cudaError_t launch_fwd_seed(int lgLEN, const uint64_t *seed, uint64_t n, uint64_t m, cx<T> *W, uint64_t L,
-                            TwTab<T> tw, cudaStream_t st);
+                            TwTab<T> tw, cudaStream_t st, bool pack = false);
 // S: innermost length (the stride of the middle strided pass).
 template <typename T>
 cudaError_t launch_mid(int lgLEN, bool inverse, cx<T> *W, uint64_t L, uint32_t S, uint32_t pairs, TwTab<T> tw,
@@ -72,7 +74,7 @@ template <typename T>
 cudaError_t launch_inv_bits(int lgLEN, const cx<T> *W, uint64_t L, uint64_t m, uint32_t nkeys,
                             const uint32_t *popc, uint32_t *margin_bits, uint64_t *out, uint64_t ostride,
                             uint32_t pairs, TwTab<T> tw, cudaStream_t st, const uint64_t *xkeys = nullptr,
-                            uint64_t xstride = 0);
+                            uint64_t xstride = 0, bool pack = false);
 
 // ---- uneven batch (complex arithmetic only: the Eq. 5-10 split needs conjugation) ----
 struct BlockDev;
@@ -95,5 +97,16 @@ cudaError_t launch_middle_split_odd(int lg, const cx<T> *Wf, cx<T> *Wi, uint64_t
 template <typename T>
 cudaError_t launch_inv_bits_blocks(int lgLEN, const cx<T> *Wi, uint64_t L, const BlockDev *blocks, uint32_t nblocks,
                                    const uint32_t *popc, uint32_t *margin_bits, TwTab<T> tw, cudaStream_t st);
+
+// ---- single keys in half-length transforms (complex arithmetic only) ----
+// Innermost pass of length ro * 2^lg over a length-N slot (slots of N elements from W):
+// mode 0 multiplies with the seed tables (3N values: E_s, O_s, w_N^k O_s, times 1/N) and
+// transforms back; mode 1 builds those tables from the packed seed's transform (scale 1/N).
+template <typename T>
+cudaError_t launch_middle_real(int ro, int lg, int mode, cx<T> *W, cx<T> *tabs, uint64_t N, uint32_t lgL1,
+                               uint32_t lgM, TwTab<T> tw, T scale, uint32_t slots, cudaStream_t st);
+template <typename T, int RO>
+cudaError_t launch_middle_real_odd(int lg, int mode, cx<T> *W, cx<T> *tabs, uint64_t N, uint32_t lgL1, uint32_t lgM,
+                                   TwTab<T> tw, T scale, uint32_t slots, cudaStream_t st);
 
 }  // namespace pa

@@ -104,3 +104,14 @@ def test_modified_argument_errors():
         pa.pa_set_seed(p.handle, to_dev(inputs.bernoulli_bits(0, 1, 1299))[0], 1299)
     assert e.value.code == pa.PA_EINVAL
     p.close()
+
+
+@pytest.mark.parametrize("dtype", [pa.PA_FP32_GUARD, pa.PA_FP64], ids=["fp32g", "fp64"])
+@pytest.mark.parametrize("n,m", [(100, 37), (65536, 6554), (100003, 40001)])
+def test_modified_single_key(n, m, dtype):
+    """A lone key of the modified hash (half-length form with the key bit offset m)."""
+    seed = inputs.bernoulli_bits(n, 3, n - 1)
+    key = inputs.batch_keys(n, 1, base_seed=n)
+    got, marg, mode, esc, _ = run(n, m, dtype, key, seed)
+    np.testing.assert_array_equal(got[0], oracle.modified_hash(n, m, seed, key[0]))
+    assert esc == 0 and marg[0] < 0.05

@@ -430,3 +430,29 @@ def test_host_buffers_three_plans_pipelined():
                                               oracle.toeplitz_rows(n, m, seed, keys[k], rows))
     for p in plans:
         p.close()
+
+
+@pytest.mark.parametrize("dtype", [pa.PA_FP32_GUARD, pa.PA_FP64], ids=["fp32g", "fp64"])
+@pytest.mark.parametrize("n,m", [(1, 1), (63, 17), (4095, 1), (5000, 1500), (131072, 32768), (100003, 40001),
+                                 (1_000_000, 500_000), ((1 << 23) + 5, (1 << 21) - 3)])
+def test_single_key_half_length_form(n, m, dtype):
+    """A lone key runs in the half-length transform (bins k, N-k split against seed tables):
+    same bits as the key paired with another one, and as the oracle."""
+    seed = inputs.bernoulli_bits(n + 3, 1, n + m - 1)
+    keys = inputs.batch_keys(n, 2, base_seed=n + 3)
+    plan = pa.Plan(n, m, dtype)
+    plan.set_seed(to_dev(seed)[0])
+    one, (marg1, mode1, esc1) = plan.hash(to_dev(keys[:1]), info=True)
+    two = plan.hash(to_dev(keys))
+    torch.cuda.synchronize()
+    plan.close()
+    w = (m + 63) // 64
+    one, two = to_host(one, w), to_host(two, w)
+    np.testing.assert_array_equal(one[0], two[0])
+    assert esc1 == 0 and marg1[0] < 0.05
+    if n <= 200_000:
+        np.testing.assert_array_equal(one[0], oracle.toeplitz_hash(n, m, seed, keys[0]))
+    else:
+        rows = sample_rows(m, 120, seed=n)
+        np.testing.assert_array_equal(unpack_rows(one, m)[0][rows.astype(np.int64)],
+                                      oracle.toeplitz_rows(n, m, seed, keys[0], rows))
