@@ -147,7 +147,10 @@ int pa_set_seed(pa_plan_t *plan, const uint64_t *seed_dev, uint64_t seed_bits, p
 /*
  * pa_hash_batch -- y_k = T x_k mod 2 for nkeys keys that share the plan's seed
  * (Eq. 3-4 for every key; two keys ride in one complex transform as its real
- * and imaginary parts, the idea of Eq. 5-10 applied to two keys).
+ * and imaginary parts, the idea of Eq. 5-10 applied to two keys). A batch of
+ * one key in PA_FP32_GUARD or PA_FP64 runs in a transform of half the length,
+ * its even and odd bits as the real and imaginary parts (Eq. 5-10's split of a
+ * complex transform into two real ones, applied per bin pair).
  *   keys_dev          device pointer; key k starts at keys_dev + k*key_stride_words
  *   nkeys             number of keys, >= 1
  *   key_stride_words  >= ceil(n/64), even (16-byte alignment of every key)
