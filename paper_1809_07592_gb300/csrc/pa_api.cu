@@ -627,24 +627,109 @@ int tune_split(pa_plan_t *p, const std::vector<Geometry> &cand) {
 
 // The half-length form of a plan: the smallest supported N with 2N >= n+m-1 whose
 // innermost pass fits the two-row kernel; left out (nullptr) if there is none.
+// Split autotuner of the half-length form (as tune_split, on one zero key, cached per
+// (N, dtype)). r->tabs must exist; the chosen split's twiddles are built by the caller.
+std::map<std::pair<uint64_t, int>, Geometry> g_real_split;
+
+template <typename T>
+int time_real(pa_plan_t *p, const uint64_t *key, uint64_t kw, uint64_t *out, uint64_t ow, cudaStream_t st,
+              cudaEvent_t a, cudaEvent_t b, float *ms) {
+    float t[6] = {};
+    for (int rep = 0; rep < 6; ++rep) {
+        PA_CUDA(cudaEventRecord(a, st));
+        int rc = run_keys_real<T>(p, key, 1, kw, out, ow, p->popc, p->marg, st);
+        if (rc != PA_OK) return rc;
+        PA_CUDA(cudaEventRecord(b, st));
+        PA_CUDA(cudaEventSynchronize(b));
+        PA_CUDA(cudaEventElapsedTime(&t[rep], a, b));
+    }
+    std::sort(t + 1, t + 6);
+    *ms = t[3];
+    return PA_OK;
+}
+
+int tune_real(pa_plan_t *p, RealMode *r) {
+    const std::pair<uint64_t, int> cache_key{r->geo.L, (int)p->dtype};
+    {
+        std::lock_guard<std::mutex> lk(g_split_mu);
+        auto it = g_real_split.find(cache_key);
+        if (it != g_real_split.end()) {
+            r->geo = it->second;
+            return PA_OK;
+        }
+    }
+    const std::vector<Geometry> cand = geometry_candidates(r->geo.L, p->dtype, true);
+    if (cand.size() < 2 || !tuning_enabled()) return PA_OK;
+    const uint64_t kw = (p->n_key + 63) / 64, ow = (p->m + 63) / 64;
+    uint64_t *key = nullptr, *out = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    auto done = [&](int rc) {
+        cudaFree(key);
+        cudaFree(out);
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+        if (st) cudaStreamDestroy(st);
+        return rc;
+    };
+    cudaError_t e = cudaMalloc(&key, kw * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&out, ow * 8);
+    if (e == cudaSuccess) e = cudaMemset(key, 0, kw * 8);
+    if (e == cudaSuccess) e = cudaMemset(r->tabs, 0, (size_t)3 * r->geo.L * elem_bytes(p->dtype));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return done(PA_ENOMEM);
+    }
+    if (e != cudaSuccess) return done(cuda_fail(e, "half-length autotuner set-up"));
+    int rc = ensure_work(p, 1);
+    if (rc == PA_OK) rc = ensure_keys(p, 1);
+    if (rc != PA_OK) return done(rc);
+    float best = 0.f;
+    Geometry bestg = r->geo;
+    for (size_t i = 0; i < cand.size(); ++i) {
+        r->geo = cand[i];
+        rc = pa_internal_twiddles(r->geo.L, r->geo.F(), (int)p->dtype, &r->tw_hi, &r->tw_lo, &r->twB, &r->tw_fine);
+        float ms = 0.f;
+        if (rc == PA_OK)
+            rc = (p->dtype == PA_FP32_GUARD) ? time_real<float>(p, key, kw, out, ow, st, a, b, &ms)
+                                             : time_real<double>(p, key, kw, out, ow, st, a, b, &ms);
+        cudaFree(r->tw_hi);
+        cudaFree(r->tw_lo);
+        cudaFree(r->tw_fine);
+        r->tw_hi = r->tw_lo = r->tw_fine = nullptr;
+        if (rc != PA_OK) return done(rc);
+        if (i == 0 || ms < best) {
+            best = ms;
+            bestg = cand[i];
+        }
+    }
+    r->geo = bestg;
+    {
+        std::lock_guard<std::mutex> lk(g_split_mu);
+        g_real_split[cache_key] = bestg;
+    }
+    return done(PA_OK);
+}
+
 int build_real_mode(pa_plan_t *p) {
     const uint64_t need = p->n + p->m - 1;
     const Geometry g = choose_geometry((need + 1) / 2, p->dtype, true);
     if (g.L == 0) return PA_OK;
     RealMode *r = new RealMode();
     r->geo = g;
-    int rc = pa_internal_twiddles(g.L, g.F(), (int)p->dtype, &r->tw_hi, &r->tw_lo, &r->twB, &r->tw_fine);
-    if (rc == PA_OK) {
-        cudaError_t e = cudaMalloc(&r->tabs, (size_t)3 * g.L * elem_bytes(p->dtype));
-        if (e == cudaErrorMemoryAllocation) {
-            cudaGetLastError();
-            rc = PA_ENOMEM;
-        } else if (e != cudaSuccess) {
-            rc = cuda_fail(e, "cudaMalloc(real tables)");
-        }
-    }
     p->real = r;  // released with the plan, also on failure
-    return rc;
+    cudaError_t e = cudaMalloc(&r->tabs, (size_t)3 * g.L * elem_bytes(p->dtype));
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return PA_ENOMEM;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(real tables)");
+    int rc = tune_real(p, r);
+    if (rc != PA_OK) return rc;
+    return pa_internal_twiddles(r->geo.L, r->geo.F(), (int)p->dtype, &r->tw_hi, &r->tw_lo, &r->twB, &r->tw_fine);
 }
 
 // pa_plan (or pa_plan_modified), with the split forced when `force` is given. For the
