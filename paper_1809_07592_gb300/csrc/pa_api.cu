@@ -1,9 +1,11 @@
 // pa_api.cu -- the C ABI declared in include/pa.h: plans, seed spectra, batched hashing.
 //
-// A plan fixes (n, m, dtype) and the transform: complex length L, a power of
-// two >= n+m-1 (paper Section 2.2: the FFT length of the standard Toeplitz
-// hash is n+r-1), split into two or three passes (paper Algorithm 1 splits a
-// long FFT into short row and column FFTs with a twiddle step in between).
+// A plan fixes (n, m, dtype) and the transform: complex length L, the smallest
+// smooth length ro * 2^k >= n+m-1 (paper Section 2.2: the FFT length of the
+// standard Toeplitz hash is n+r-1), split into two or three passes (paper
+// Algorithm 1 splits a long FFT into short row and column FFTs with a twiddle
+// step in between), the split chosen by timing every candidate. Key pairs share
+// one complex transform; a lone key uses a half-length one (RealMode).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
