@@ -283,6 +283,35 @@ def measure_serving(pa, inputs, torch, dev, rate=5000.0, seconds=1.0):
             "escalated": st["escalated"], "mode": "FP32_GUARD"}
 
 
+def measure_single_block(pa, inputs, torch, dev, reps=20):
+    """The plain single block: n = 131072, m = 32768, one key, seed spectrum resident, FP64 and FP32_GUARD."""
+    n, m = 131072, 32768
+    key, seed = inputs.block_inputs(n, m, base_seed=0)
+    kd, sd = _dev_words(torch, key, dev), _dev_words(torch, seed, dev)
+    ow = (m + 63) // 64
+    out = torch.empty((1, ow + (ow & 1)), dtype=torch.int64, device=dev)
+    res = {}
+    stream = torch.cuda.current_stream()
+    for name, dt in (("fp64", pa.PA_FP64), ("fp32_guard", pa.PA_FP32_GUARD)):
+        plan = pa.Plan(n, m, dt)
+        plan.set_seed(sd)
+        for _ in range(3):
+            pa.pa_hash_batch(plan.handle, kd.view(1, -1), 1, kd.numel(), out, out.shape[1], stream)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pa.pa_hash_batch(plan.handle, kd.view(1, -1), 1, kd.numel(), out, out.shape[1], stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        ms = statistics.median(ts)
+        res[name] = {"value": n / (ms * 1e-3) / 1e6, "unit": "Mbit/s", "ms": ms}
+        plan.close()
+    return res
+
+
 def measure_long_block(pa, inputs, torch, dev, reps=3):
     """n = 2^27, m = 2^24 (transform length 2^28), one block, seed spectrum resident, per mode."""
     n, m = 1 << 27, 1 << 24
@@ -531,6 +560,12 @@ def run_ours(args):
     if rank == 0 and not args.headline_only:
         extra["uneven_256_blocks"] = measure_uneven(pa, inputs, torch, dev)
         extra["serving"] = measure_serving(pa, inputs, torch, dev)
+        extra["serving_rates"] = {}
+        for rate in (200.0, 1000.0, 2000.0):
+            sv = measure_serving(pa, inputs, torch, dev, rate=rate, seconds=1.0 if rate >= 1000 else 2.0)
+            extra["serving_rates"][str(int(rate))] = {k: sv[k] for k in ("value", "p50_ms", "p99_ms", "max_ms",
+                                                                        "requests")}
+        extra["single_block_131072"] = measure_single_block(pa, inputs, torch, dev)
         extra["long_block_2p27"] = measure_long_block(pa, inputs, torch, dev)
         extra["modified_toeplitz"] = measure_modified(pa, inputs, torch, dev)
 
