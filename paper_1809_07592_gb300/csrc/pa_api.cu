@@ -459,6 +459,16 @@ int run_keys(pa_plan_t *p, const uint64_t *keys, uint32_t nkeys, uint64_t kstrid
     return PA_OK;
 }
 
+void free_real_mode(pa_plan_t *p) {
+    if (!p->real) return;
+    cudaFree(p->real->tw_hi);
+    cudaFree(p->real->tw_lo);
+    cudaFree(p->real->tw_fine);
+    cudaFree(p->real->tabs);
+    delete p->real;
+    p->real = nullptr;
+}
+
 void free_plan(pa_plan_t *p) {
     if (!p) return;
     if (p->fallback) free_plan(p->fallback);
@@ -473,13 +483,7 @@ void free_plan(pa_plan_t *p) {
     cudaFree(p->seed_copy);
     if (p->h_marg) cudaFreeHost(p->h_marg);
     if (p->done) cudaEventDestroy(p->done);
-    if (p->real) {
-        cudaFree(p->real->tw_hi);
-        cudaFree(p->real->tw_lo);
-        cudaFree(p->real->tw_fine);
-        cudaFree(p->real->tabs);
-        delete p->real;
-    }
+    free_real_mode(p);
     cudaFree(p->stage_keys);
     cudaFree(p->stage_out);
     if (p->ev_in) cudaEventDestroy(p->ev_in);
@@ -777,7 +781,12 @@ int plan_create(uint64_t n, uint64_t m, pa_dtype_t dtype, const Geometry *force,
         if (cand.size() > 1) rc = tune_split(p, cand);
     }
     if (rc == PA_OK) rc = build_plan_twiddles(p);
-    if (rc == PA_OK && dtype != PA_NTT64) rc = build_real_mode(p);
+    if (rc == PA_OK && dtype != PA_NTT64 && build_real_mode(p) != PA_OK) {
+        // The half-length form is an optimisation: without memory for its tables a lone
+        // key takes the pair form instead.
+        free_real_mode(p);
+        cudaGetLastError();
+    }
     if (rc != PA_OK) {
         free_plan(p);
         return rc;
