@@ -289,6 +289,78 @@ def measure_serving(pa, inputs, torch, dev, rate=5000.0, seconds=1.0):
             "escalated": st["escalated"], "mode": "FP32_GUARD"}
 
 
+def measure_cufft_comparison(pa, inputs, torch, dev, reps=10):
+    """Comparison point only (not the product): the same DV-QKD step written with torch.fft (cuFFT)
+    and torch elementwise ops -- bit unpack, real FFT of the 64 keys, product with the cached seed
+    spectrum, inverse real FFT, rounding, parity, bit pack -- at the library's transform lengths, with
+    the same +-1 seed encoding. Output bits of key 0 of every batch are checked against the library."""
+    stream = torch.cuda.current_stream()
+    shifts = torch.arange(64, device=dev, dtype=torch.int64)
+    weights = (2 ** torch.arange(8, device=dev, dtype=torch.int32)).to(torch.uint8)
+    cases = []
+    for n, m in subconfigs():
+        seed = inputs.bernoulli_bits(0, inputs.STREAM_SEED, n + m - 1)
+        keys = inputs.batch_keys(n, NKEYS, base_seed=0)
+        plan = pa.Plan(n, m, pa.PA_FP32_GUARD)
+        L = plan.shape()[0]
+        sd = _dev_words(torch, seed, dev)
+        plan.set_seed(sd)
+        kw = keys.shape[1] + (keys.shape[1] & 1)
+        kb = np.zeros((NKEYS, kw), np.uint64)
+        kb[:, : keys.shape[1]] = keys
+        dk = torch.from_numpy(kb.view(np.int64)).to(dev)
+        ow = (m + 63) // 64
+        ref = plan.hash(dk)[:1, :ow].clone()
+        plan.close()
+        sbits = ((torch.from_numpy(seed.view(np.int64)).to(dev).unsqueeze(-1) >> shifts) & 1).flatten()[: n + m - 1]
+        sigma = torch.zeros(L, device=dev, dtype=torch.float32)
+        sigma[: n + m - 1] = 1.0 - 2.0 * sbits.to(torch.float32)
+        S = torch.fft.rfft(sigma)
+        cases.append(dict(n=n, m=m, L=L, dk=dk, S=S, ref=ref, ow=ow))
+
+    def one(c):
+        n, m, L = c["n"], c["m"], c["L"]
+        x = ((c["dk"].unsqueeze(-1) >> shifts) & 1).flatten(1)[:, :n].to(torch.float32)  # 0/1 key bits
+        r = torch.fft.irfft(torch.fft.rfft(x, n=L) * c["S"], n=L)[:, n - 1: n - 1 + m]  # r = P - 2c
+        P = x.sum(dim=1, keepdim=True)
+        y = torch.remainder(torch.round((P - r) * 0.5), 2.0).to(torch.uint8)
+        pad = torch.zeros((NKEYS, c["ow"] * 64), device=dev, dtype=torch.uint8)
+        pad[:, :m] = y
+        packed = (pad.view(NKEYS, -1, 8) * weights).sum(dim=-1, dtype=torch.uint8)
+        return packed.view(torch.int64)
+
+    ok = all(torch.equal(one(c)[:1], c["ref"]) for c in cases)
+    for _ in range(3):
+        for c in cases:
+            one(c)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for c in cases:
+            one(c)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    ms = statistics.median(ts)
+    # the transforms alone (keys already unpacked to floats): rfft, product, irfft
+    xs = [((c["dk"].unsqueeze(-1) >> shifts) & 1).flatten(1)[:, : c["n"]].to(torch.float32) for c in cases]
+    tf = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for c, x in zip(cases, xs):
+            torch.fft.irfft(torch.fft.rfft(x, n=c["L"]) * c["S"], n=c["L"])
+        b.record(stream)
+        torch.cuda.synchronize()
+        tf.append(a.elapsed_time(b))
+    bits = sum(c["n"] for c in cases) * NKEYS
+    return {"value": bits / (ms * 1e-3) / 1e6, "unit": "Mbit/s", "ms_per_step": ms, "bits_match_library": ok,
+            "transforms_only_ms_per_step": statistics.median(tf),
+            "form": "torch.fft (cuFFT) real transforms + torch elementwise ops, comparison point only"}
+
+
 def measure_single_block(pa, inputs, torch, dev, reps=20):
     """The plain single block: n = 131072, m = 32768, one key, seed spectrum resident, FP64 and FP32_GUARD."""
     n, m = 131072, 32768
@@ -572,6 +644,7 @@ def run_ours(args):
             extra["serving_rates"][str(int(rate))] = {k: sv[k] for k in ("value", "p50_ms", "p99_ms", "max_ms",
                                                                         "requests")}
         extra["single_block_131072"] = measure_single_block(pa, inputs, torch, dev)
+        extra["cufft_comparison"] = measure_cufft_comparison(pa, inputs, torch, dev)
         extra["long_block_2p27"] = measure_long_block(pa, inputs, torch, dev)
         extra["modified_toeplitz"] = measure_modified(pa, inputs, torch, dev)
 
