@@ -163,26 +163,37 @@ def algorithmic_bytes(kind: str, n: int, m: int, L: int, pairs: int, nkeys: int,
     return 0.0
 
 
+def _oracle_keys(oracle, inputs, threads, key_index, row_fraction=1):
+    """The oracle on key `key_index` of each of the six (n, m) batches of the workload (the same
+    seed and keys as the GPU step), rows [0, m / row_fraction) of each. Returns (key bits, seconds
+    scaled to whole keys)."""
+    bits, secs = 0, 0.0
+    for n, m in subconfigs():
+        seed = inputs.bernoulli_bits(0, inputs.STREAM_SEED, n + m - 1)
+        key = inputs.batch_keys(n, 1, base_seed=0, first_stream=2 + key_index)[0]  # key key_index of the batch
+        rows = max(64, m // row_fraction - (m // row_fraction) % 64) if row_fraction > 1 else m
+        t0 = time.perf_counter()
+        oracle.toeplitz_row_range(n, m, seed, key, 0, rows, threads)
+        secs += (time.perf_counter() - t0) * m / rows
+        bits += n
+    return bits, secs
+
+
 def cpu_baseline(budget_s: float = 12.0):
-    """The oracle, as it stands, on a bounded sample: rows of key 0 of (n=2^20, m=n/4), scaled to a whole key."""
+    """The oracle, as it stands, on a bounded sample of the workload: whole keys of the six (n, m)
+    batches (key 0 of each, then key 1, ...) until about budget_s seconds of CPU work."""
     from oracle import oracle
     from paper_1809_07592_gb300 import inputs
-    n, m = 1 << 20, 1 << 18
-    key, seed = inputs.block_inputs(n, m, base_seed=0, key_stream=2)
     threads = os.cpu_count() or 1
-    rows = 1024
-    t0 = time.perf_counter()
-    oracle.toeplitz_row_range(n, m, seed, key, 0, rows, threads)
-    dt = time.perf_counter() - t0
-    rows = int(min(m, max(rows, rows * budget_s / max(dt, 1e-6))))
-    rows -= rows % 64
-    t0 = time.perf_counter()
-    oracle.toeplitz_row_range(n, m, seed, key, 0, rows, threads)
-    dt = time.perf_counter() - t0
-    per_key = dt * m / rows
-    return {"value": n / per_key / 1e6, "unit": "Mbit/s", "cores": threads, "kind": "oracle",
-            "sample": f"key 0 of n=1048576, m=262144: rows 0..{rows - 1} of {m} in {dt:.2f} s, scaled to all rows",
-            "seconds": round(dt, 3)}
+    bits, secs, k = 0, 0.0, 0
+    while secs < budget_s and k < NKEYS:
+        b, t = _oracle_keys(oracle, inputs, threads, k)
+        bits += b
+        secs += t
+        k += 1
+    return {"value": bits / secs / 1e6, "unit": "Mbit/s", "cores": threads, "kind": "oracle",
+            "sample": f"keys 0..{k - 1} of each of the six (n, m) batches, every row, in {secs:.2f} s",
+            "seconds": round(secs, 3)}
 
 
 def run_reference(args):
@@ -192,27 +203,24 @@ def run_reference(args):
     from oracle import oracle
     from paper_1809_07592_gb300 import inputs
     threads = os.cpu_count() or 1
-    n, m = 1 << 20, 1 << 18
-    key, seed = inputs.block_inputs(n, m, base_seed=0, key_stream=2)
-    rows = 1024
-    oracle.toeplitz_row_range(n, m, seed, key, 0, 256, threads)  # build + warm
+    frac = 8  # each step: the first eighth of the rows of one key of every (n, m) batch
+    _oracle_keys(oracle, inputs, threads, 0, row_fraction=64)  # build + warm
     for _ in range(args.warmup):
-        oracle.toeplitz_row_range(n, m, seed, key, 0, 256, threads)
-    times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        oracle.toeplitz_row_range(n, m, seed, key, 0, rows, threads)
-        times.append((time.perf_counter() - t0) * m / rows)  # seconds per whole key
-    per_key = statistics.median(times)
-    value = n / per_key / 1e6
+        _oracle_keys(oracle, inputs, threads, 0, row_fraction=frac)
+    times, bits = [], 0
+    for s in range(args.steps):
+        bits, secs = _oracle_keys(oracle, inputs, threads, s % NKEYS, row_fraction=frac)
+        times.append(secs)  # seconds for one whole key of each batch
+    per_step = statistics.median(times)
+    value = bits / per_step / 1e6
     line = {"metric": METRIC, "value": value, "unit": "Mbit/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": per_key * 1e3, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": "one key of n=1048576, m=262144 per step"},
+            "config": {"workload": WORKLOAD, "sample": "one key of each of the six (n, m) batches per step"},
             "impl": "reference",
             "cpu_baseline": {"kind": "oracle", "cores": threads, "value": value, "unit": "Mbit/s",
-                             "sample": f"rows 0..{rows - 1} of key 0 (n=1048576, m=262144) per step, "
-                                       f"scaled to all {m} rows"},
+                             "sample": f"rows 0..m/{frac} of key s of each of the six (n, m) batches per step s, "
+                                       "scaled to all rows"},
             "e2e": {"value": value, "unit": "Mbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -504,25 +512,40 @@ def run_ours(args):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
     stream = torch.cuda.current_stream()
 
-    def step(end_event=None):
+    # The batches of a step alternate between two streams: while one batch's short tail
+    # launches drain, the next batch's first pass already fills the SMs.
+    sides = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)]
+
+    def join_sides():
+        for sd in sides:
+            stream.wait_stream(sd)
+
+    def step(end_event=None, overlap=True):
         # Every batch is issued before the first guard step runs, so the GPU sees the six
-        # batches back to back. end_event is recorded behind the last batch (its kernels and
-        # margin read-back); the guard steps then run on the host. If a guard recomputes
+        # batches back to back (batch i on side stream i % 2, both after the main stream's
+        # work so far). end_event is recorded on the main stream behind every batch (its kernels
+        # and margin read-back); the guard steps then run on the host. If a guard recomputes
         # any key, that work is issued after end_event, so the step then ends at an event
-        # recorded behind it (returned as the second value).
+        # recorded behind it (returned as the second value). overlap=False keeps every batch on
+        # one stream, so that per-launch events time each kernel alone.
+        for sd in sides:
+            sd.wait_stream(stream)
         lat = []
-        for c in cases:
+        for i, c in enumerate(cases):
+            sd = sides[i % 2] if overlap else sides[0]
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            pa.pa_hash_batch_async(c["plan"].handle, c["dk"], NKEYS, c["kw"], c["out"], c["ow"], stream)
-            b.record(stream)
+            a.record(sd)
+            pa.pa_hash_batch_async(c["plan"].handle, c["dk"], NKEYS, c["kw"], c["out"], c["ow"], sd)
+            b.record(sd)
             lat.append((a, b))
+        join_sides()
         if end_event is not None:
             end_event.record(stream)
         escalated = 0
         for c in cases:
             escalated += pa.pa_batch_finish(c["plan"].handle, NKEYS, info=True)[2]
+        join_sides()
         late_end = None
         if escalated and end_event is not None:
             late_end = torch.cuda.Event(enable_timing=True)
@@ -565,7 +588,7 @@ def run_ours(args):
     for _ in range(prof_steps):
         flush.zero_()
         barrier()
-        step()
+        step(overlap=False)
     barrier()
     prof = {}
     for c in cases:
@@ -623,10 +646,13 @@ def run_ours(args):
         s0 = torch.cuda.Event(enable_timing=True)
         s1 = torch.cuda.Event(enable_timing=True)
         s0.record(stream)
-        for c in cases:
-            pa.pa_hash_host_async(c["plan"].handle, c["hk"], NKEYS, c["kw"], c["ho"], c["ow"], stream)
+        for sd in sides:
+            sd.wait_stream(stream)
+        for i, c in enumerate(cases):
+            pa.pa_hash_host_async(c["plan"].handle, c["hk"], NKEYS, c["kw"], c["ho"], c["ow"], sides[i % 2])
         for c in cases:
             pa.pa_batch_finish(c["plan"].handle)
+        join_sides()
         s1.record(stream)
         torch.cuda.synchronize()
         if it >= args.warmup:
@@ -658,10 +684,10 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": list(N_VALUES), "m_over_n": list(RATIOS), "keys_per_batch": NKEYS,
                        "batches_per_step": len(cases), "mode": "FP32_GUARD", "transform_lengths": lengths,
-                       "pass_splits": splits,
+                       "pass_splits": splits, "streams": len(sides),
                        "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas{world}"},
             "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
-            "batch_latency_ms": {"p50": p50, "p99": p99, "unit": "ms per 64-key batch"},
+            "batch_latency_ms": {"p50": p50, "p99": p99, "unit": "ms per 64-key batch, two batches in flight"},
             "fp64_plain": {"value": fp64_value, "unit": "Mbit/s",
                            "form": "single key per call, FP64 transforms, same (n, m) set"},
             "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -21,8 +21,11 @@
  * negative PA_E* codes below; pa_strerror() names them. No C++ exception crosses
  * this boundary. Device pointers must be 16-byte aligned.
  *
- * Threads: a plan may be used from one host thread at a time; calls on one plan
- * must be issued to one stream at a time. A server is thread-safe.
+ * Threads: a plan may be used from one host thread at a time. Its calls may take
+ * different streams: each batch or seed upload first waits (on the device) for the
+ * plan's previous one, so the calls on one plan run in issue order whatever
+ * stream carries them, while different plans on different streams overlap.
+ * A server is thread-safe.
  */
 #ifndef PA_H_
 #define PA_H_

@@ -832,6 +832,9 @@ int issue_batch(pa_plan_t *p, const uint64_t *keys_dev, uint32_t nkeys, uint64_t
     rc = ensure_host(p, nkeys);
     if (rc != PA_OK) return rc;
     if (!p->done) PA_CUDA(cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming));
+    // The plan's work buffers are shared by its batches: a batch issued on another stream
+    // than the previous one waits for it (a no-op on the same stream).
+    PA_CUDA(cudaStreamWaitEvent(st, p->done, 0));
     if (p->dtype == PA_FP32_GUARD)
         rc = run_keys<float>(p, keys_dev, nkeys, kstride, out_dev, ostride, p->popc, p->marg, st);
     else if (p->dtype == PA_FP64)
@@ -1019,6 +1022,8 @@ int pa_set_seed(pa_plan_t *p, const uint64_t *seed_dev, uint64_t seed_bits, pa_s
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     int rc = ensure_work(p, 1);
     if (rc != PA_OK) return rc;
+    if (!p->done) PA_CUDA(cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming));
+    PA_CUDA(cudaStreamWaitEvent(st, p->done, 0));  // after the plan's previous work, on any stream
     const size_t sw = (size_t)((seed_bits + 63) / 64);
     if (!p->seed_copy) PA_CUDA(cudaMalloc(&p->seed_copy, sw * sizeof(uint64_t)));
     PA_CUDA(cudaMemcpyAsync(p->seed_copy, seed_dev, sw * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
@@ -1033,6 +1038,7 @@ int pa_set_seed(pa_plan_t *p, const uint64_t *seed_dev, uint64_t seed_bits, pa_s
         if (rc != PA_OK) return rc;
         p->real->seeded = true;
     }
+    PA_CUDA(cudaEventRecord(p->done, st));
     p->seeded = true;
     if (p->fallback) p->fallback->seeded = false;  // re-seeded lazily on the next escalation
     return PA_OK;

@@ -456,3 +456,34 @@ def test_single_key_half_length_form(n, m, dtype):
         rows = sample_rows(m, 120, seed=n)
         np.testing.assert_array_equal(unpack_rows(one, m)[0][rows.astype(np.int64)],
                                       oracle.toeplitz_rows(n, m, seed, keys[0], rows))
+
+
+@pytest.mark.parametrize("dtype", [pa.PA_FP64, pa.PA_NTT64], ids=["fp64", "ntt64"])
+def test_plan_on_several_streams(dtype):
+    """One plan driven from three streams with no host wait in between (FP64 and NTT64 return
+    right after issuing): batches, and a seed change between them, run in issue order."""
+    n, m, nk = 1 << 20, 1 << 18, 6
+    seeds = [inputs.bernoulli_bits(90 + s, 1, n + m - 1) for s in range(2)]
+    keys = [inputs.batch_keys(n, nk, base_seed=90 + b) for b in range(4)]
+    plan = pa.Plan(n, m, dtype)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()]
+    dseeds = [to_dev(s)[0] for s in seeds]
+    dkeys = [to_dev(k) for k in keys]
+    ow = (m + 63) // 64
+    outs = [torch.full((nk, ow), -1, dtype=torch.int64, device="cuda") for _ in keys]
+    torch.cuda.synchronize()
+    plan.set_seed(dseeds[0], stream=streams[2])
+    for b in range(4):
+        if b == 2:
+            plan.set_seed(dseeds[1], stream=streams[1])
+        st = streams[b % 3]
+        pa.pa_hash_batch(plan.handle, dkeys[b], nk, dkeys[b].shape[1], outs[b], ow, st)
+    torch.cuda.synchronize()
+    plan.close()
+    rows = sample_rows(m, 80, seed=9)
+    for b in range(4):
+        seed = seeds[0] if b < 2 else seeds[1]
+        got = unpack_rows(to_host(outs[b], ow), m)
+        for k in (0, nk - 1):
+            np.testing.assert_array_equal(got[k][rows.astype(np.int64)],
+                                          oracle.toeplitz_rows(n, m, seed, keys[b][k], rows))
