@@ -433,6 +433,45 @@ __device__ __forceinline__ uint32_t idx_e(uint32_t tq, int s) {
     return tq + (uint32_t)s * (LEN / E);
 }
 
+__host__ __device__ constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
+
+// Shared-memory slot of element a of a contiguous row (one column) at a stage
+// boundary of span SPAN (the reading stage's span: the writing stage has P * R = SPAN).
+// Power-of-two spans (every boundary of a power-of-two row, and the inverse
+// transform's) use the skew of sidx. A row with an odd stage of radix RC writes
+// with strides RC and R * RC in the forward transform, which that skew leaves
+// 2-4-way bank conflicted; those boundaries (spans divisible by RC) pad one slot
+// every lcm(RC, W) elements instead (W = elements per 128 bytes), and the first one
+// keeps the plain index when RC is odd (an odd stride is conflict-free as it is).
+template <typename T, int LEN, int E, int SPAN>
+__device__ __forceinline__ uint32_t ridx(uint32_t a) {
+    constexpr int RC = Plan<LEN, E>::RC;
+    if constexpr (RC > 1 && SPAN % RC == 0) {
+        if constexpr (RC % 2 == 1) {
+            if constexpr (SPAN == RC) {
+                return a;
+            } else {
+                return a + (a >> 4);
+            }
+        } else {
+            constexpr int W = 128 / (int)sizeof(cx<T>);
+            constexpr uint32_t D = (uint32_t)(RC / gcd_c(RC, W) * W);  // lcm(RC, W) >= 16: fits smem_elems
+            return a + a / D;
+        }
+    } else {
+        return a + (a >> 4);
+    }
+}
+// Slot at a stage boundary: ridx for rows, sidx for interleaved columns.
+template <typename T, int LEN, int COLS, int E, int SPAN>
+__device__ __forceinline__ uint32_t bslot(uint32_t a, uint32_t col) {
+    if constexpr (COLS == 1) {
+        return ridx<T, LEN, E, SPAN>(a);
+    } else {
+        return sidx<COLS>(a, col);
+    }
+}
+
 // One Stockham stage of radix R at span P, from registers (already loaded
 // with this stage's inputs) to shared memory. Thread tq handles the E/R
 // butterfly groups i = tq + b*TC; group i reads elements i + r*LEN/R,
@@ -449,19 +488,20 @@ __device__ __forceinline__ void stage_to_smem(cx<T> *sm, cx<T> *v, uint32_t tq, 
         dft<T, R, INV>(v + b * R);
         const uint32_t base = (i - k) * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) sm[sidx<COLS>(base + (uint32_t)r * P, col)] = v[b * R + r];
+        for (int r = 0; r < R; ++r) sm[bslot<T, LEN, COLS, E, P * R>(base + (uint32_t)r * P, col)] = v[b * R + r];
     }
 }
 
-// Load a stage's inputs from shared memory: group i = tq + b*TC, elements i + r*LEN/R.
-template <typename T, int LEN, int COLS, int E, int R>
+// Load a stage's inputs from shared memory: group i = tq + b*TC, elements i + r*LEN/R
+// (boundary of span SPAN, the reading stage's span).
+template <typename T, int LEN, int COLS, int E, int R, int SPAN>
 __device__ __forceinline__ void load_from_smem(const cx<T> *sm, cx<T> *v, uint32_t tq, uint32_t col) {
     constexpr int TC = LEN / E;
 #pragma unroll
     for (int b = 0; b < E / R; ++b) {
         const uint32_t i = tq + (uint32_t)b * TC;
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[b * R + r] = sm[sidx<COLS>(i + (uint32_t)r * (LEN / R), col)];
+        for (int r = 0; r < R; ++r) v[b * R + r] = sm[bslot<T, LEN, COLS, E, SPAN>(i + (uint32_t)r * (LEN / R), col)];
     }
 }
 
@@ -487,7 +527,7 @@ __device__ __forceinline__ void fwd_pow2(cx<T> *sm, cx<T> *v, uint32_t tq, uint3
     constexpr int R = (S == 0) ? PL::r0 : E;
     if constexpr (!FROM_REGS) {
         __syncthreads();
-        load_from_smem<T, LEN, COLS, E, R>(sm, v, tq, col);
+        load_from_smem<T, LEN, COLS, E, R, P0>(sm, v, tq, col);
     }
     if constexpr (S == PL::q - 1) {
         stage_in_regs<T, LEN, COLS, E, R, P0, false>(v, tq, tw);
@@ -510,7 +550,7 @@ __device__ __forceinline__ void inv_pow2(cx<T> *sm, cx<T> *v, uint32_t tq, uint3
     constexpr int R = (S == PL::q - 1) ? PL::r0 : E;
     if constexpr (S > 0) {
         __syncthreads();
-        load_from_smem<T, LEN, COLS, E, R>(sm, v, tq, col);
+        load_from_smem<T, LEN, COLS, E, R, P0>(sm, v, tq, col);
     }
     if constexpr (S == LAST && !TO_SMEM) {
         stage_in_regs<T, LEN, COLS, E, R, P0, true>(v, tq, tw);
@@ -555,7 +595,7 @@ __device__ __forceinline__ void odd_first_stage(cx<T> *sm, uint32_t tq, Ld ld) {
             for (int r = 0; r < RC; ++r) u[r] = ld(g + (uint32_t)r * K);
             dft_comp<T, PL::RO, PL::R0C, false>(u);
 #pragma unroll
-            for (int r = 0; r < RC; ++r) sm[sidx<1>(g * RC + (uint32_t)r, 0)] = u[r];
+            for (int r = 0; r < RC; ++r) sm[ridx<T, LEN, E, RC>(g * RC + (uint32_t)r)] = u[r];
         }
     }
 }
@@ -589,7 +629,7 @@ __device__ __forceinline__ void cta_fft_inv_odd(cx<T> *sm, cx<T> *v, uint32_t tq
         if (g < (uint32_t)K) {
             cx<T> u[RC];
 #pragma unroll
-            for (int r = 0; r < RC; ++r) u[r] = sm[sidx<1>(g + (uint32_t)r * K, 0)];
+            for (int r = 0; r < RC; ++r) u[r] = sm[ridx<T, LEN, E, K>(g + (uint32_t)r * K)];
             stage_twiddles<T, true, RC>(u, tw, g * (tw.F / LEN));
             dft_comp<T, PL::RO, PL::R0C, true>(u);
 #pragma unroll
