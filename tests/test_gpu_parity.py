@@ -487,3 +487,56 @@ def test_plan_on_several_streams(dtype):
         for k in (0, nk - 1):
             np.testing.assert_array_equal(got[k][rows.astype(np.int64)],
                                           oracle.toeplitz_rows(n, m, seed, keys[b][k], rows))
+
+
+@pytest.mark.parametrize("host", [False, True], ids=["device", "host"])
+def test_dv_qkd_step_on_two_streams(host):
+    """The benchmark's step as it is timed: the six DV-QKD batches (64 keys each, one seed per
+    (n, m)) issued back to back alternating between two streams, then finished; device-resident
+    buffers, or host buffers through pa_hash_host_async. Sampled rows of keys 0, 33 and 63 of
+    every batch vs the oracle, and every key's rows equal to the same batch run alone."""
+    nk = 64
+    sides = [torch.cuda.Stream(), torch.cuda.Stream()]
+    cases = []
+    for n in (1_000_000, 1 << 20):
+        for ratio in (0.1, 0.25, 0.5):
+            m = int(ratio * n)
+            seed = inputs.bernoulli_bits(0, inputs.STREAM_SEED, n + m - 1)
+            keys = inputs.batch_keys(n, nk, base_seed=0)
+            p = pa.Plan(n, m, pa.PA_FP32_GUARD)
+            p.set_seed(to_dev(seed)[0])
+            kw = keys.shape[1] + (keys.shape[1] & 1)
+            ow = (m + 63) // 64 + ((m + 63) // 64 & 1)
+            if host:
+                ki = _host_rows(keys, kw, True)
+                out = torch.zeros((nk, ow), dtype=torch.int64).pin_memory()
+            else:
+                ki = to_dev(keys, kw)
+                out = torch.full((nk, ow), -1, dtype=torch.int64, device="cuda")
+            cases.append(dict(n=n, m=m, seed=seed, keys=keys, plan=p, ki=ki, out=out, kw=kw, ow=ow))
+    torch.cuda.synchronize()
+    main = torch.cuda.current_stream()
+    for sd in sides:
+        sd.wait_stream(main)
+    for i, c in enumerate(cases):
+        issue = pa.pa_hash_host_async if host else pa.pa_hash_batch_async
+        issue(c["plan"].handle, c["ki"], nk, c["kw"], c["out"], c["ow"], sides[i % 2])
+    for c in cases:
+        marg, mode, esc = pa.pa_batch_finish(c["plan"].handle, nk, info=True)
+        assert esc == 0 and max(marg) < 0.05
+    for sd in sides:
+        main.wait_stream(sd)
+    torch.cuda.synchronize()
+    for c in cases:
+        n, m = c["n"], c["m"]
+        w = (m + 63) // 64
+        got = (c["out"].numpy() if host else c["out"].cpu().numpy()).view(np.uint64)[:, :w]
+        alone = to_host(c["plan"].hash(to_dev(c["keys"], c["kw"])), w)
+        np.testing.assert_array_equal(got, alone, err_msg=f"(n, m) = ({n}, {m}): two-stream step vs alone")
+        rows = sample_rows(m, 60, seed=m)
+        bits = unpack_rows(got[[0, 33, 63]], m)
+        for j, k in enumerate((0, 33, 63)):
+            np.testing.assert_array_equal(bits[j][rows.astype(np.int64)],
+                                          oracle.toeplitz_rows(n, m, c["seed"], c["keys"][k], rows),
+                                          err_msg=f"(n, m) = ({n}, {m}), key {k}")
+        c["plan"].close()
