@@ -84,3 +84,52 @@ def test_security_parameter_helpers_without_gpu():
     assert math.isclose(pa.pa_leakage_bound(1000, 400, 600), 1 / math.log(2), rel_tol=1e-12)
     # the bound halves for every bit dropped from the final key
     assert math.isclose(pa.pa_leakage_bound(5000, 1000, 3900) / pa.pa_leakage_bound(5000, 1000, 3901), 0.5)
+
+
+def test_plan_lengths_and_splits_sweep_without_gpu():
+    """Plan invariants over 240 seeded (n, m), host only: every split multiplies out to the one
+    transform length L >= n+m-1; L is smooth (odd part 1, 3, 5 or 9; a power of two for the exact
+    mode); the strided passes are powers of two in [64, 1024] and the odd factor sits in the
+    innermost pass; and from n+m-1 = 24576 on (the smallest smooth length a split can realise:
+    a 64-point strided pass times a 3 * 128-point innermost row) L is the smallest length of the
+    ladder {1, 3, 5, 9} * 2^k (odd factors with k >= 13) not below n+m-1."""
+    import random
+
+    import paper_1809_07592_gb300 as pa
+    build.build()
+    rng = random.Random(17)
+
+    def odd(v):
+        while v % 2 == 0:
+            v //= 2
+        return v
+
+    def ladder_min(need, exact):
+        best = 1 << 40
+        for ro in ((1,) if exact else (1, 3, 5, 9)):
+            k = 0 if ro == 1 else 13
+            while (ro << k) < need:
+                k += 1
+            best = min(best, ro << k)
+        return best
+
+    for _ in range(80):
+        n = max(1, int(2 ** rng.uniform(4, 27)))
+        m = max(1, int(rng.uniform(0.01, 1.0) * n))
+        need = n + m - 1
+        for dtype in (pa.PA_FP32_GUARD, pa.PA_FP64, pa.PA_NTT64):
+            splits = pa.pa_plan_splits(n, m, dtype)
+            assert splits, (n, m, dtype)
+            lengths = {a * b * c for a, b, c in splits}
+            assert len(lengths) == 1, (n, m, dtype, splits)
+            L = lengths.pop()
+            exact = dtype == pa.PA_NTT64
+            assert need <= L <= 1 << 28 and L >= 4096
+            assert odd(L) in ((1,) if exact else (1, 3, 5, 9)), (n, m, dtype, L)
+            for a, b, c in splits:
+                inner = b if c == 1 else c
+                strided = (a,) if c == 1 else (a, b)
+                assert all(s & (s - 1) == 0 and 64 <= s <= 1024 for s in strided), splits
+                assert odd(inner) == odd(L), splits
+            if need >= 24576:
+                assert L == ladder_min(need, exact), (n, m, dtype, L, ladder_min(need, exact))
