@@ -21,6 +21,13 @@
  * negative PA_E* codes below; pa_strerror() names them. No C++ exception crosses
  * this boundary. Device pointers must be 16-byte aligned.
  *
+ * Environment (read when a plan or batch is built; all optional):
+ *   PA_PLAN_TUNE=0    take the default pass split instead of timing every split
+ *   PA_TUNE_CACHE     file that keeps the uneven batches' tuned splits across processes
+ *   PA_WORK_BYTES     work-buffer budget of one launch chunk in bytes (default 4 GiB): a
+ *                     batch whose key pairs need more runs in several chunks
+ *   PA_POW2_ONLY      (any value) restrict transform lengths to powers of two
+ *
  * Threads: a plan may be used from one host thread at a time. Its calls may take
  * different streams: each batch or seed upload first waits (on the device) for the
  * plan's previous one, so the calls on one plan run in issue order whatever
