@@ -159,7 +159,7 @@ def algorithmic_bytes(kind: str, n: int, m: int, L: int, pairs: int, nkeys: int,
     if kind in ("mid_fwd", "mid_inv"):
         return 2 * pairs * slot
     if kind == "prep":
-        return nkeys * kw
+        return nkeys * 8  # popcount and margin words reset
     return 0.0
 
 
