@@ -163,19 +163,31 @@ def algorithmic_bytes(kind: str, n: int, m: int, L: int, pairs: int, nkeys: int,
     return 0.0
 
 
-def _oracle_keys(oracle, inputs, threads, key_index, row_fraction=1):
-    """The oracle on key `key_index` of each of the six (n, m) batches of the workload (the same
-    seed and keys as the GPU step), rows [0, m / row_fraction) of each. Returns (key bits, seconds
-    scaled to whole keys)."""
+def workload_config(world: int) -> dict:
+    """The workload both arms report (the reference arm runs a bounded sample of it)."""
+    return {"workload": WORKLOAD, "n": list(N_VALUES), "m_over_n": list(RATIOS), "keys_per_batch": NKEYS,
+            "batches_per_step": len(subconfigs()), "mode": "FP32_GUARD",
+            "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas{world}"}
+
+
+def _oracle_key(oracle, inputs, threads, batch, key_index):
+    """The oracle on the whole of key `key_index` of batch `batch` of the workload (the same seed and
+    key as the GPU step), every row. Returns (key bits, seconds)."""
+    n, m = subconfigs()[batch]
+    seed = inputs.bernoulli_bits(0, inputs.STREAM_SEED, n + m - 1)
+    key = inputs.batch_keys(n, 1, base_seed=0, first_stream=2 + key_index)[0]  # key key_index of the batch
+    t0 = time.perf_counter()
+    oracle.toeplitz_hash(n, m, seed, key, threads)
+    return n, time.perf_counter() - t0
+
+
+def _oracle_keys(oracle, inputs, threads, key_index):
+    """Whole key `key_index` of each of the six (n, m) batches. Returns (key bits, seconds)."""
     bits, secs = 0, 0.0
-    for n, m in subconfigs():
-        seed = inputs.bernoulli_bits(0, inputs.STREAM_SEED, n + m - 1)
-        key = inputs.batch_keys(n, 1, base_seed=0, first_stream=2 + key_index)[0]  # key key_index of the batch
-        rows = max(64, m // row_fraction - (m // row_fraction) % 64) if row_fraction > 1 else m
-        t0 = time.perf_counter()
-        oracle.toeplitz_row_range(n, m, seed, key, 0, rows, threads)
-        secs += (time.perf_counter() - t0) * m / rows
-        bits += n
+    for b in range(len(subconfigs())):
+        nb, sb = _oracle_key(oracle, inputs, threads, b, key_index)
+        bits += nb
+        secs += sb
     return bits, secs
 
 
@@ -203,24 +215,26 @@ def run_reference(args):
     from oracle import oracle
     from paper_1809_07592_gb300 import inputs
     threads = os.cpu_count() or 1
-    frac = 8  # each step: the first eighth of the rows of one key of every (n, m) batch
-    _oracle_keys(oracle, inputs, threads, 0, row_fraction=64)  # build + warm
-    for _ in range(args.warmup):
-        _oracle_keys(oracle, inputs, threads, 0, row_fraction=frac)
+    nb = len(subconfigs())
+    # every step hashes one whole key, every row, with the oracle: step s takes key s // 6 of
+    # batch s % 6, so consecutive steps walk through the six (n, m) batches; the warm-up steps
+    # (which also build the oracle) take keys from the other end of each batch
+    for w in range(args.warmup):
+        _oracle_key(oracle, inputs, threads, w % nb, NKEYS - 1 - (w // nb) % NKEYS)
     times, bits = [], 0
     for s in range(args.steps):
-        bits, secs = _oracle_keys(oracle, inputs, threads, s % NKEYS, row_fraction=frac)
-        times.append(secs)  # seconds for one whole key of each batch
-    per_step = statistics.median(times)
-    value = bits / per_step / 1e6
+        b, t = _oracle_key(oracle, inputs, threads, s % nb, (s // nb) % NKEYS)
+        bits += b
+        times.append(t)
+    total = sum(times)
+    value = bits / total / 1e6
     line = {"metric": METRIC, "value": value, "unit": "Mbit/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": "one key of each of the six (n, m) batches per step"},
-            "impl": "reference",
+            "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": workload_config(world), "impl": "reference",
             "cpu_baseline": {"kind": "oracle", "cores": threads, "value": value, "unit": "Mbit/s",
-                             "sample": f"rows 0..m/{frac} of key s of each of the six (n, m) batches per step s, "
-                                       "scaled to all rows"},
+                             "sample": "one whole key (every row) per step: step s hashes key s // 6 of the "
+                                       "(n, m) batch s % 6", "seconds": round(total, 3)},
             "e2e": {"value": value, "unit": "Mbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -682,10 +696,8 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "Mbit/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": list(N_VALUES), "m_over_n": list(RATIOS), "keys_per_batch": NKEYS,
-                       "batches_per_step": len(cases), "mode": "FP32_GUARD", "transform_lengths": lengths,
-                       "pass_splits": splits, "streams": len(sides),
-                       "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas{world}"},
+            "config": workload_config(world),
+            "plans": {"transform_lengths": lengths, "pass_splits": splits, "streams": len(sides)},
             "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
             "batch_latency_ms": {"p50": p50, "p99": p99, "unit": "ms per 64-key batch, two batches in flight"},
             "fp64_plain": {"value": fp64_value, "unit": "Mbit/s",

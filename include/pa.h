@@ -27,6 +27,8 @@
  *   PA_WORK_BYTES     work-buffer budget of one launch chunk in bytes (default 4 GiB): a
  *                     batch whose key pairs need more runs in several chunks
  *   PA_POW2_ONLY      (any value) restrict transform lengths to powers of two
+ *   PA_STATIC_GUARD   rounding-margin threshold of pa_hash_static's guard (default 0.25;
+ *                     read at every call; a negative value forces its escalation path)
  *
  * Threads: a plan may be used from one host thread at a time. Its calls may take
  * different streams: each batch or seed upload first waits (on the device) for the
@@ -230,6 +232,22 @@ int pa_hash_host(pa_plan_t *plan, const uint64_t *keys_host, uint32_t nkeys, uin
  */
 int pa_plan_set_guard(pa_plan_t *plan, float threshold);
 
+/*
+ * pa_plan_expire_waits -- test hook for the device-side wait limit (library robustness;
+ * the paper has no counterpart). The pipelined convolution kernel (the innermost pass of
+ * PA_FP32_GUARD plans whose rows hold 3072 to 4608 values) waits for each bulk copy with
+ * a time limit; when a wait runs out the kernel sets bit 0 of the plan's device error
+ * word and returns instead of spinning. After this call, the next `launches` launches of
+ * that kernel issue no copy and wait 10 microseconds on a barrier phase that nothing can
+ * complete, so their wait runs out with no copy in flight. The batch's synchronising call
+ * (pa_hash_batch of a PA_FP32_GUARD plan or with info, pa_hash_host, pa_batch_finish)
+ * then returns PA_ETIMEOUT and clears the word; that batch's outputs are not valid, and
+ * the plan stays usable. Every other call reports such an error only at the next
+ * synchronising call on the plan. Returns PA_EUNSUPPORTED for plans whose innermost
+ * pass does not use the pipelined kernel, PA_EINVAL for a NULL plan.
+ */
+int pa_plan_expire_waits(pa_plan_t *plan, uint32_t launches);
+
 /* Plan introspection (no GPU work): transform length L and pass lengths L1, L2, L3 (L3 = 1 for two passes). */
 int pa_plan_shape(const pa_plan_t *plan, uint64_t *L, uint32_t *L1, uint32_t *L2, uint32_t *L3);
 
@@ -250,8 +268,9 @@ typedef struct {
 typedef struct pa_uneven pa_uneven_t;
 
 /*
- * pa_uneven_create -- plan an uneven batch. Blocks are grouped by transform length
- * L = 2^ceil(log2(n+m-1)) (at least 2^12); every class gets its own work buffers, twiddle
+ * pa_uneven_create -- plan an uneven batch. Blocks are grouped by transform length L, the
+ * smallest smooth length ro * 2^k >= max(n+m-1, 2^12) with ro in {1, 3, 5, 9} (PA_NTT64:
+ * powers of two only), as pa_plan chooses it; every class gets its own work buffers, twiddle
  * tables and a device copy of its block descriptors, and its pass split is chosen by the
  * built-in autotuner (timed on the class's own buffers, cached per (L, dtype) for the process
  * and, if the environment variable PA_TUNE_CACHE names a file, across processes).
@@ -393,7 +412,9 @@ int pa_profile_read(pa_plan_t *plan, pa_kernel_stat_t *stats, int *count, int re
  * margin, if not NULL, receives the larger rounding margin of the keys (host).
  *
  * The first call on a device looks up the array's device address on that device
- * (cudaGetSymbolAddress); make that first call before any stream capture. Every
+ * (cudaGetSymbolAddress) and keeps it for that device's context; a call after the
+ * context was reset (cudaDeviceReset) looks it up again. Make the first call on a
+ * device, and the first after a reset, before any stream capture. Every
  * call re-transforms the seed and reuses the same array, which keeps the last
  * call's contents: calls that overlap on the GPU (different streams, or threads)
  * race and must be serialised by the caller. PA_FP32_GUARD calls, and any call

@@ -97,6 +97,7 @@ def lib():
     L.pa_set_seed.argtypes = [vp, vp, u64, vp]
     L.pa_hash_batch.argtypes = [vp, vp, u32, u64, vp, u64, vp, ctypes.POINTER(BatchInfo)]
     L.pa_plan_set_guard.argtypes = [vp, ctypes.c_float]
+    L.pa_plan_expire_waits.argtypes = [vp, u32]
     L.pa_hash_batch_async.argtypes = [vp, vp, u32, u64, vp, u64, vp]
     L.pa_batch_finish.argtypes = [vp, ctypes.POINTER(BatchInfo)]
     L.pa_hash_host_async.argtypes = [vp, vp, u32, u64, vp, u64, vp]
@@ -222,6 +223,11 @@ def pa_plan_destroy(plan: int) -> None:
 
 def pa_plan_set_guard(plan: int, threshold: float) -> None:
     _check(lib().pa_plan_set_guard(plan, threshold), "pa_plan_set_guard")
+
+
+def pa_plan_expire_waits(plan: int, launches: int = 1) -> None:
+    """Test hook: the next `launches` pipelined convolution launches let their bounded wait run out."""
+    _check(lib().pa_plan_expire_waits(plan, launches), "pa_plan_expire_waits")
 
 
 def pa_plan_shape(plan: int):

@@ -102,6 +102,7 @@ struct pa_plan {
     uint32_t *popc = nullptr;    // per key
     uint32_t *marg = nullptr;    // per key, float bits
     uint32_t *err = nullptr;     // device word: bit 0 = a bounded copy wait ran out of time
+    uint32_t expire_launches = 0;  // test hook: pipelined launches left whose first wait is made to run out
     uint32_t key_cap = 0;
     float *h_marg = nullptr;     // pinned: h_cap margins, then the error word
     uint32_t h_cap = 0;
@@ -417,6 +418,15 @@ int run_keys_real(pa_plan_t *p, const uint64_t *keys, uint32_t nkeys, uint64_t k
     return PA_OK;
 }
 
+// Wait limit handed to the next pipelined convolution launch: 0 (the kernel's own 1 s
+// limit, copies issued as usual), or, while the test hook of pa_plan_expire_waits is
+// armed, 10 us on a barrier phase that no copy completes.
+uint32_t take_expire(pa_plan_t *p) {
+    if (p->expire_launches == 0) return 0u;
+    --p->expire_launches;
+    return 10000u;
+}
+
 template <typename T>
 int run_keys(pa_plan_t *p, const uint64_t *keys, uint32_t nkeys, uint64_t kstride, uint64_t *out,
              uint64_t ostride, uint32_t *popc, uint32_t *marg, cudaStream_t st) {
@@ -448,11 +458,11 @@ int run_keys(pa_plan_t *p, const uint64_t *keys, uint32_t nkeys, uint64_t kstrid
         { Timed t_(p, K_FWD_KEYS, st); PA_CUDA(launch_fwd_keys<T>(g.lg1, kp, nk, kstride, p->n, W, p->L, pairs, tw, popc + k0, st, p->koff)); }
         if (g.lgM) {
             { Timed t_(p, K_MID_FWD, st); PA_CUDA(launch_mid<T>(g.lgM, false, W, p->L, g.inner(), pairs, tw, st)); }
-            { Timed t_(p, K_MIDDLE_CONV, st); PA_CUDA(launch_middle<T>(g.ro, g.lgI, 0, W, spec, p->L, pairs, tw, one<T>(), st, p->err)); }
+            { Timed t_(p, K_MIDDLE_CONV, st); PA_CUDA(launch_middle<T>(g.ro, g.lgI, 0, W, spec, p->L, pairs, tw, one<T>(), st, p->err, take_expire(p))); }
             { Timed t_(p, K_MID_INV, st); PA_CUDA(launch_mid<T>(g.lgM, true, W, p->L, g.inner(), pairs, tw, st)); }
         } else {
             Timed t_(p, K_MIDDLE_CONV, st);
-            PA_CUDA(launch_middle<T>(g.ro, g.lgI, 0, W, spec, p->L, pairs, tw, one<T>(), st, p->err));
+            PA_CUDA(launch_middle<T>(g.ro, g.lgI, 0, W, spec, p->L, pairs, tw, one<T>(), st, p->err, take_expire(p)));
         }
         { Timed t_(p, K_INV_BITS, st); PA_CUDA(launch_inv_bits<T>(g.lg1, W, p->L, p->m, nk, popc + k0, marg + k0, op, ostride, pairs, tw, st, p->modified ? kp : nullptr, kstride)); }
     }
@@ -983,6 +993,15 @@ int pa_plan_shape(const pa_plan_t *p, uint64_t *L, uint32_t *L1, uint32_t *L2, u
 int pa_plan_set_guard(pa_plan_t *p, float threshold) {
     if (!p) return PA_EINVAL;
     p->guard = threshold;
+    return PA_OK;
+}
+
+int pa_plan_expire_waits(pa_plan_t *p, uint32_t launches) {
+    if (!p) return PA_EINVAL;
+    const Geometry &g = p->geo;
+    if (p->dtype != PA_FP32_GUARD || !pipe_fits(g.inner(), elem_bytes(p->dtype))) return PA_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lk(p->mu);
+    p->expire_launches = launches;
     return PA_OK;
 }
 

@@ -348,10 +348,13 @@ __global__ void __launch_bounds__(LEN / E, min_blocks_inner(LEN / E, sizeof(cx<T
 // seed-spectrum row is copied only when the row changes. The arithmetic is
 // k_middle's, step for step. A copy wait that runs out of time sets bit 0 of
 // *err and the CTA returns (after a bounded wait for its copies in flight).
+// expire_ns != 0 is a test hook for that error path: the CTA issues no copy at
+// all and waits expire_ns on a barrier phase that nothing can complete, so the
+// wait runs out with no copy in flight, sets the error bit and returns.
 template <typename T, int LEN, int E>
 __global__ void __launch_bounds__(LEN / E, min_blocks_inner(LEN / E, sizeof(cx<T>)))
     k_middle_pipe(cx<T> *__restrict__ W, const cx<T> *__restrict__ spec, uint64_t L, uint32_t pairs,
-                  uint32_t tiles_per_cta, TwTab<T> tw, uint32_t *__restrict__ err) {
+                  uint32_t tiles_per_cta, TwTab<T> tw, uint32_t *__restrict__ err, uint32_t expire_ns) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     constexpr uint32_t kRowBytes = LEN * sizeof(cx<T>);
     static_assert(kRowBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
@@ -370,12 +373,18 @@ __global__ void __launch_bounds__(LEN / E, min_blocks_inner(LEN / E, sizeof(cx<T
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         mbar_init_fence();
-        mbar_arrive_expect_tx(&bar[0], kRowBytes);
-        bulk_load(stg, row_of(t0), kRowBytes, &bar[0]);
-        mbar_arrive_expect_tx(&bar[1], kRowBytes);
-        bulk_load(ssp, spec + (uint64_t)srow * LEN, kRowBytes, &bar[1]);
+        if (expire_ns == 0) {
+            mbar_arrive_expect_tx(&bar[0], kRowBytes);
+            bulk_load(stg, row_of(t0), kRowBytes, &bar[0]);
+            mbar_arrive_expect_tx(&bar[1], kRowBytes);
+            bulk_load(ssp, spec + (uint64_t)srow * LEN, kRowBytes, &bar[1]);
+        }
     }
     __syncthreads();
+    if (expire_ns != 0) {  // test hook: phase 0 of bar[0] has no arrival and no copy, so it never completes
+        if (tq == 0 && !mbar_wait(&bar[0], 0, expire_ns)) atomicOr(err, 1u);
+        return;
+    }
     uint32_t pd = 0, ps = 0;
     bool spec_wait = true;
     for (uint32_t t = t0; t < t1; ++t) {
@@ -453,8 +462,8 @@ template <> struct BitsWord<32> { using type = uint32_t; };
 __device__ __forceinline__ float margin_to_float(float x) { return x; }
 __device__ __forceinline__ float margin_to_float(double x) { return __double2float_ru(x); }
 
-// Level-1 inverse pass with the post-processing of the paper's Fig. 2
-// ("rounds the result of IFFT to Boolean sequence"): round, mod 2, pack.
+// Level-1 inverse pass with the post-processing step of the paper's Fig. 2 (the
+// inverse transform's output rounded to integers, then reduced mod 2): round, mod 2, pack.
 // Output bit i = element i of the convolution window; bits >= m are written 0.
 // Each key's rounding margin max |w - rint(w)| goes to margin_bits (float bits,
 // atomicMax; all margins are >= 0 so integer order equals float order).

@@ -133,7 +133,8 @@ constexpr size_t pipe_smem_bytes() {
 }
 template <typename T, int LEN>
 constexpr bool pipe_ok() {
-    return LEN >= 3072 && pipe_smem_bytes<T, LEN>() <= 112 * 1024;
+    static_assert(pipe_smem_bytes<T, LEN>() == (3 * (size_t)LEN + LEN / 16 + 1) * sizeof(cx<T>), "pipe_fits formula");
+    return pipe_fits(LEN, sizeof(cx<T>));
 }
 
 // Persistent grid of k_middle_pipe: resident CTAs per SM (occupancy query) times the
@@ -160,7 +161,7 @@ cudaError_t persistent_ctas(K kern, int threads, size_t smem, int *cache, uint32
 
 template <typename T, int LEN>
 cudaError_t middle_at(int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pairs, TwTab<T> tw, cx<T> scale,
-                      cudaStream_t st, uint32_t *err) {
+                      cudaStream_t st, uint32_t *err, uint32_t expire_ns) {
     constexpr int E = Shape<T>::E;
     constexpr size_t sb = smem_bytes<T, LEN, 1>();
     dim3 grid((unsigned)(L / LEN), pairs);
@@ -178,7 +179,7 @@ cudaError_t middle_at(int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pair
             if (ntiles > 0xFFFFFFFFull) return cudaErrorInvalidValue;
             const uint32_t per = (uint32_t)((ntiles + ctas - 1) / ctas);
             const uint32_t nct = (uint32_t)((ntiles + per - 1) / per);
-            kern<<<nct, LEN / E, pb, st>>>(W, spec, L, pairs, per, tw, err);
+            kern<<<nct, LEN / E, pb, st>>>(W, spec, L, pairs, per, tw, err, expire_ns);
             return cudaGetLastError();
         }
     }
@@ -198,18 +199,18 @@ cudaError_t middle_at(int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pair
 
 template <typename T>
 cudaError_t launch_middle(int ro, int lg, int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pairs, TwTab<T> tw,
-                          cx<T> scale, cudaStream_t st, uint32_t *err) {
+                          cx<T> scale, cudaStream_t st, uint32_t *err, uint32_t expire_ns) {
     if (ro == 1) {
         return by_len<kMinLgMiddle, MaxLgMiddle<T>::v>(lg, [&](auto c) {
-            return middle_at<T, decltype(c)::value>(mode, W, spec, L, pairs, tw, scale, st, err);
+            return middle_at<T, decltype(c)::value>(mode, W, spec, L, pairs, tw, scale, st, err, expire_ns);
         });
     }
     if constexpr (std::is_same<T, Zp>::value) {
         return cudaErrorInvalidValue;  // the exact transform keeps power-of-two lengths
     } else {
-        if (ro == 3) return launch_middle_odd<T, 3>(lg, mode, W, spec, L, pairs, tw, scale, st, err);
-        if (ro == 5) return launch_middle_odd<T, 5>(lg, mode, W, spec, L, pairs, tw, scale, st, err);
-        if (ro == 9) return launch_middle_odd<T, 9>(lg, mode, W, spec, L, pairs, tw, scale, st, err);
+        if (ro == 3) return launch_middle_odd<T, 3>(lg, mode, W, spec, L, pairs, tw, scale, st, err, expire_ns);
+        if (ro == 5) return launch_middle_odd<T, 5>(lg, mode, W, spec, L, pairs, tw, scale, st, err, expire_ns);
+        if (ro == 9) return launch_middle_odd<T, 9>(lg, mode, W, spec, L, pairs, tw, scale, st, err, expire_ns);
         return cudaErrorInvalidValue;
     }
 }
@@ -217,25 +218,25 @@ cudaError_t launch_middle(int ro, int lg, int mode, cx<T> *W, cx<T> *spec, uint6
 // Odd innermost lengths RO * 2^lg, lg in [kMinLgOdd, kMaxLgOdd], where the CTA fits.
 template <typename T, int RO, int LG = kMinLgOdd>
 cudaError_t odd_middle_dispatch(int lg, int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pairs, TwTab<T> tw,
-                                cx<T> scale, cudaStream_t st, uint32_t *err) {
+                                cx<T> scale, cudaStream_t st, uint32_t *err, uint32_t expire_ns) {
     if constexpr (LG > kMaxLgOdd) {
         return cudaErrorInvalidValue;
     } else {
         if (lg == LG) {
             if constexpr (odd_inner_ok<T>(RO, LG, false)) {
-                return middle_at<T, RO * (1 << LG)>(mode, W, spec, L, pairs, tw, scale, st, err);
+                return middle_at<T, RO * (1 << LG)>(mode, W, spec, L, pairs, tw, scale, st, err, expire_ns);
             } else {
                 return cudaErrorInvalidValue;
             }
         }
-        return odd_middle_dispatch<T, RO, LG + 1>(lg, mode, W, spec, L, pairs, tw, scale, st, err);
+        return odd_middle_dispatch<T, RO, LG + 1>(lg, mode, W, spec, L, pairs, tw, scale, st, err, expire_ns);
     }
 }
 
 template <typename T, int RO>
 cudaError_t launch_middle_odd(int lg, int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pairs, TwTab<T> tw,
-                              cx<T> scale, cudaStream_t st, uint32_t *err) {
-    return odd_middle_dispatch<T, RO>(lg, mode, W, spec, L, pairs, tw, scale, st, err);
+                              cx<T> scale, cudaStream_t st, uint32_t *err, uint32_t expire_ns) {
+    return odd_middle_dispatch<T, RO>(lg, mode, W, spec, L, pairs, tw, scale, st, err, expire_ns);
 }
 
 template <typename T, int LEN, bool PACK>
@@ -280,7 +281,7 @@ cudaError_t launch_inv_bits(int lgLEN, const cx<T> *W, uint64_t L, uint64_t m, u
     template cudaError_t launch_mid<T>(int, bool, cx<T> *, uint64_t, uint32_t, uint32_t, TwTab<T>,               \
                                        cudaStream_t);                                                           \
     template cudaError_t launch_middle<T>(int, int, int, cx<T> *, cx<T> *, uint64_t, uint32_t, TwTab<T>, cx<T>,  \
-                                          cudaStream_t, uint32_t *);                                            \
+                                          cudaStream_t, uint32_t *, uint32_t);                                  \
     template cudaError_t launch_inv_bits<T>(int, const cx<T> *, uint64_t, uint64_t, uint32_t, const uint32_t *,  \
                                             uint32_t *, uint64_t *, uint64_t, uint32_t, TwTab<T>, cudaStream_t,  \
                                             const uint64_t *, uint64_t, bool);
@@ -440,7 +441,7 @@ cudaError_t launch_middle_real(int ro, int lg, int mode, cx<T> *W, cx<T> *tabs, 
 // Odd innermost lengths of one (type, RO): the plain middle pass and the split pass.
 #define PA_INSTANTIATE_ODD(T, RO)                                                                               \
     template cudaError_t launch_middle_odd<T, RO>(int, int, cx<T> *, cx<T> *, uint64_t, uint32_t, TwTab<T>,     \
-                                                  cx<T>, cudaStream_t, uint32_t *);                             \
+                                                  cx<T>, cudaStream_t, uint32_t *, uint32_t);                   \
     template cudaError_t launch_middle_split_odd<T, RO>(int, const cx<T> *, cx<T> *, uint64_t, uint32_t,        \
                                                         uint32_t, uint32_t, TwTab<T>, cudaStream_t);            \
     template cudaError_t launch_middle_real_odd<T, RO>(int, int, cx<T> *, cx<T> *, uint64_t, uint32_t, uint32_t, \

@@ -53,13 +53,21 @@ cudaError_t launch_mid(int lgLEN, bool inverse, cx<T> *W, uint64_t L, uint32_t S
 // Innermost pass of length ro * 2^lg. mode 0: the fused convolution step; mode 1:
 // the seed spectrum. With err != nullptr, mode 0 runs the persistent pipelined
 // kernel where its shared memory fits, and a copy wait that runs out of time sets
-// bit 0 of *err (device memory).
+// bit 0 of *err (device memory). expire_ns != 0 (test hook) makes that kernel issue
+// no copy and let its first wait run out after expire_ns.
 template <typename T>
 cudaError_t launch_middle(int ro, int lg, int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pairs, TwTab<T> tw,
-                          cx<T> scale, cudaStream_t st, uint32_t *err = nullptr);
+                          cx<T> scale, cudaStream_t st, uint32_t *err = nullptr, uint32_t expire_ns = 0);
 template <typename T, int RO>
 cudaError_t launch_middle_odd(int lg, int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pairs, TwTab<T> tw,
-                              cx<T> scale, cudaStream_t st, uint32_t *err);
+                              cx<T> scale, cudaStream_t st, uint32_t *err, uint32_t expire_ns);
+
+// Whether the fused convolution step of a row of `len` elements of `elem_bytes` bytes
+// runs as the persistent pipelined kernel (k_middle_pipe): rows of at least 3072
+// elements whose two staging rows and exchange buffer fit 112 KB of shared memory.
+constexpr bool pipe_fits(uint64_t len, uint64_t elem_bytes) {
+    return len >= 3072 && (2 * len + len + len / 16 + 1) * elem_bytes <= 112 * 1024;
+}
 
 // Limits of the odd innermost lengths RO * 2^lg: a CTA has RO * 2^lg / E threads
 // (at most 1024, or 512 per row for the two-row split kernel).

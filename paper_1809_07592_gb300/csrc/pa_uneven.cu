@@ -1,6 +1,7 @@
 // pa_uneven.cu -- uneven batches: blocks of different (n, m), each with its own seed.
 //
-// Blocks are grouped into classes by transform length L = 2^ceil(log2(n+m-1)).
+// Blocks are grouped into classes by transform length L, the smallest smooth
+// length ro * 2^k >= n+m-1 (ro in {1, 3, 5, 9}; powers of two in the exact mode).
 // Complex modes use the paper's real-valued FFT acceleration (Eq. 5-10): key and
 // seed of a block ride in one complex transform z = x + i*sigma, the fused
 // innermost pass separates their spectra from the bin pair (k, -k), multiplies

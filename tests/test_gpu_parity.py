@@ -6,7 +6,7 @@ import torch
 import paper_1809_07592_gb300 as pa
 from oracle import oracle
 from paper_1809_07592_gb300 import inputs
-from tests.gpu_util import sample_rows, to_dev, to_host, unpack_rows
+from tests.gpu_util import cover_rows, sample_rows, to_dev, to_host, unpack_rows
 
 pytestmark = pytest.mark.gpu
 
@@ -162,7 +162,7 @@ def test_three_level_plan(dtype):
     key, seed = inputs.block_inputs(n, m, base_seed=77)
     got, marg, mode, esc, shape = run(n, m, dtype, key[None, :], seed)
     assert shape[3] > 1
-    rows = sample_rows(m, 200, seed=1)
+    rows = cover_rows(m, shape)
     exp = oracle.toeplitz_rows(n, m, seed, key, rows)
     np.testing.assert_array_equal(unpack_rows(got, m)[0][rows.astype(np.int64)], exp)
     assert marg[0] < 0.1
@@ -171,15 +171,19 @@ def test_three_level_plan(dtype):
 @pytest.mark.parametrize("n", [1_000_000, 1 << 20])
 @pytest.mark.parametrize("ratio", [0.1, 0.25, 0.5])
 def test_dv_qkd_block_64_keys(n, ratio):
-    """64 keys sharing one seed at the DV-QKD block sizes; FP32-guarded, sampled rows vs the oracle."""
+    """64 keys sharing one seed at the DV-QKD block sizes, FP32-guarded: the first and the last key
+    (the real part of the first transform, the imaginary part of the last) whole vs the oracle,
+    three more keys on rows that cover every digit of the plan's split."""
     m = int(ratio * n)
     seed = inputs.bernoulli_bits(0, 1, n + m - 1)
     keys = inputs.batch_keys(n, 64, base_seed=0)
-    got, marg, mode, esc, _ = run(n, m, pa.PA_FP32_GUARD, keys, seed)
+    got, marg, mode, esc, shape = run(n, m, pa.PA_FP32_GUARD, keys, seed)
     assert esc == 0 and (marg < 0.05).all()
-    bits = unpack_rows(got[[0, 1, 31, 62, 63]], m)
-    rows = sample_rows(m, 150, seed=n)
-    for j, k in enumerate([0, 1, 31, 62, 63]):
+    for k in (0, 63):
+        np.testing.assert_array_equal(got[k], oracle.toeplitz_hash(n, m, seed, keys[k]), err_msg=f"key {k}")
+    bits = unpack_rows(got[[1, 31, 62]], m)
+    rows = cover_rows(m, shape, count=8192)
+    for j, k in enumerate([1, 31, 62]):
         exp = oracle.toeplitz_rows(n, m, seed, keys[k], rows)
         np.testing.assert_array_equal(bits[j][rows.astype(np.int64)], exp, err_msg=f"key {k}")
 
@@ -218,7 +222,7 @@ def test_long_block_2p27(dtype):
     assert n + m - 1 <= shape[0] <= 1 << 28 and shape[3] > 1
     if dtype == pa.PA_NTT64:
         assert shape[0] == 1 << 28  # the exact transform keeps power-of-two lengths
-    rows = sample_rows(m, 120, seed=27)
+    rows = cover_rows(m, shape)
     exp = oracle.toeplitz_rows(n, m, seed, key, rows)
     np.testing.assert_array_equal(unpack_rows(got, m)[0][rows.astype(np.int64)], exp)
     if dtype == pa.PA_FP32_GUARD:
@@ -256,7 +260,7 @@ def test_smooth_three_level(dtype):
     key, seed = inputs.block_inputs(n, m, base_seed=31)
     got, marg, mode, esc, shape = run(n, m, dtype, key[None, :], seed)
     assert shape[0] == 3 << 23 and shape[3] > 1
-    rows = sample_rows(m, 150, seed=3)
+    rows = cover_rows(m, shape)
     exp = oracle.toeplitz_rows(n, m, seed, key, rows)
     np.testing.assert_array_equal(unpack_rows(got, m)[0][rows.astype(np.int64)], exp)
 
@@ -493,8 +497,8 @@ def test_plan_on_several_streams(dtype):
 def test_dv_qkd_step_on_two_streams(host):
     """The benchmark's step as it is timed: the six DV-QKD batches (64 keys each, one seed per
     (n, m)) issued back to back alternating between two streams, then finished; device-resident
-    buffers, or host buffers through pa_hash_host_async. Sampled rows of keys 0, 33 and 63 of
-    every batch vs the oracle, and every key's rows equal to the same batch run alone."""
+    buffers, or host buffers through pa_hash_host_async. Keys 0 and 63 of every batch whole vs the
+    oracle, sampled rows of key 33, and every key equal to the same batch run alone."""
     nk = 64
     sides = [torch.cuda.Stream(), torch.cuda.Stream()]
     cases = []
@@ -533,10 +537,11 @@ def test_dv_qkd_step_on_two_streams(host):
         got = (c["out"].numpy() if host else c["out"].cpu().numpy()).view(np.uint64)[:, :w]
         alone = to_host(c["plan"].hash(to_dev(c["keys"], c["kw"])), w)
         np.testing.assert_array_equal(got, alone, err_msg=f"(n, m) = ({n}, {m}): two-stream step vs alone")
-        rows = sample_rows(m, 60, seed=m)
-        bits = unpack_rows(got[[0, 33, 63]], m)
-        for j, k in enumerate((0, 33, 63)):
-            np.testing.assert_array_equal(bits[j][rows.astype(np.int64)],
-                                          oracle.toeplitz_rows(n, m, c["seed"], c["keys"][k], rows),
+        for k in (0, 63):
+            np.testing.assert_array_equal(got[k], oracle.toeplitz_hash(n, m, c["seed"], c["keys"][k]),
                                           err_msg=f"(n, m) = ({n}, {m}), key {k}")
+        rows = sample_rows(m, 300, seed=m)
+        np.testing.assert_array_equal(unpack_rows(got[[33]], m)[0][rows.astype(np.int64)],
+                                      oracle.toeplitz_rows(n, m, c["seed"], c["keys"][33], rows),
+                                      err_msg=f"(n, m) = ({n}, {m}), key 33")
         c["plan"].close()

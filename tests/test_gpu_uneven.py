@@ -6,7 +6,7 @@ import torch
 import paper_1809_07592_gb300 as pa
 from oracle import oracle
 from paper_1809_07592_gb300 import inputs
-from tests.gpu_util import sample_rows, to_dev, to_host, unpack_rows
+from tests.gpu_util import cover_rows, sample_rows, to_dev, to_host, unpack_rows
 
 pytestmark = pytest.mark.gpu
 
@@ -32,13 +32,23 @@ def device_blocks(sizes, data):
     return blocks
 
 
-def check_blocks(sizes, data, blocks, full_limit=400_000, nrows=200):
+def class_shape(h, n, m):
+    """(L, L1, L2, L3) of the class that holds a block: the smallest class length >= n + m - 1
+    (a block's class is the smallest smooth length that fits it, and every class length is smooth)."""
+    fits = [c for c in pa.pa_uneven_classes(h) if c[0] >= n + m - 1]
+    c = min(fits, key=lambda c: c[0])
+    return (c[0], c[1], c[2], c[3])
+
+
+def check_blocks(sizes, data, blocks, full_limit=400_000, nrows=200, h=None):
+    """Blocks with n <= full_limit whole vs the oracle; larger ones on nrows rows (covering every digit
+    of their class's split when the batch handle h is given, else sampled)."""
     for b, ((n, m), (k, s), blk) in enumerate(zip(sizes, data, blocks)):
         got = blk[4].cpu().numpy().view(np.uint64)[: (m + 63) // 64]
         if n <= full_limit:
             np.testing.assert_array_equal(got, oracle.toeplitz_hash(n, m, s, k), err_msg=f"block {b} n={n} m={m}")
         else:
-            rows = sample_rows(m, nrows, seed=b)
+            rows = cover_rows(m, class_shape(h, n, m), count=nrows) if h is not None else sample_rows(m, nrows, seed=b)
             exp = oracle.toeplitz_rows(n, m, s, k, rows)
             np.testing.assert_array_equal(unpack_rows(got[None, :], m)[0][rows.astype(np.int64)], exp,
                                           err_msg=f"block {b} n={n} m={m}")
@@ -76,7 +86,7 @@ def test_uneven_three_level_class(dtype):
     marg, mode, esc = pa.pa_uneven_run(h, len(blocks), info=True)
     torch.cuda.synchronize()
     assert any(c[3] > 1 for c in pa.pa_uneven_classes(h))  # at least one three-level class
-    check_blocks(sizes, data, blocks)
+    check_blocks(sizes, data, blocks, nrows=65536, h=h)
     assert esc == 0 and max(marg) < 0.125  # transform length 2^24: well inside the 0.25 guard
     pa.pa_uneven_destroy(h)
 
@@ -135,7 +145,6 @@ def test_uneven_256_block_workload():
     marg, mode, esc = pa.pa_uneven_run(h, len(blocks), info=True)
     torch.cuda.synchronize()
     assert esc == 0 and max(marg) < 0.2  # lengths up to 2^25 with the Eq. 5-10 split; guard is 0.25
-    pick = [0, 1, 17, 100, 128, 200, 254, 255]
-    check_blocks([sizes[i] for i in pick], [data[i] for i in pick], [blocks[i] for i in pick], full_limit=0,
-                 nrows=60)
+    # every block with n <= 2^20 whole, the larger ones on rows covering every digit of their split
+    check_blocks(sizes, data, blocks, full_limit=1 << 20, nrows=2048, h=h)
     pa.pa_uneven_destroy(h)
