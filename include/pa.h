@@ -233,18 +233,47 @@ int pa_hash_host(pa_plan_t *plan, const uint64_t *keys_host, uint32_t nkeys, uin
 int pa_plan_set_guard(pa_plan_t *plan, float threshold);
 
 /*
+ * pa_plan_set_staged -- run the last pass of this plan's batches (on = 1) as a persistent
+ * kernel that stages its input tiles in shared memory with tiled asynchronous copies (the
+ * TMA) while it transforms the previous tile, or (on = 0, the default) as one CTA per tile
+ * with plain loads. Applies to PA_FP32_GUARD plans whose first pass length is at most 256
+ * (other plans ignore it). Both give the same bits. Measured on the DV-QKD batches: the
+ * staged pass is about 6 % faster when one batch runs alone, but a step whose batches
+ * overlap on two streams is about 2 % slower with it, because the persistent kernel holds
+ * its SMs while the other stream's kernels wait. No counterpart in the paper.
+ */
+int pa_plan_set_staged(pa_plan_t *plan, int on);
+
+/*
+ * pa_plan_set_storage_bits -- reduced-precision storage study (the paper's Section 5 asks
+ * how far the FFT's precision can go down before privacy amplification breaks). With
+ * 1 <= bits <= 22, every value a PA_FP32_GUARD plan stores between its passes (the key
+ * transforms after each pass, and the seed spectrum) is rounded to `bits` explicit
+ * significand bits, round to nearest even, as if it were kept in a narrower format with
+ * FP32's exponent range (10 bits: FP16's significand; 7: BF16's); the arithmetic inside
+ * each pass stays FP32. Each rounding is one extra elementwise pass over the slots, so
+ * this is a measurement mode, not a fast one. Margins grow accordingly, the guard
+ * escalates every key whose margin exceeds its threshold, and the output bits stay exact.
+ * bits = 23 (or 0) turns it off. The call discards the cached seed spectrum: call
+ * pa_set_seed again before hashing. Batches of this plan use key pairs only (a lone key
+ * does not take the half-length form). PA_EUNSUPPORTED for other modes, PA_EINVAL for
+ * bits > 23. No counterpart in the paper's method itself.
+ */
+int pa_plan_set_storage_bits(pa_plan_t *plan, uint32_t bits);
+
+/*
  * pa_plan_expire_waits -- test hook for the device-side wait limit (library robustness;
- * the paper has no counterpart). The pipelined convolution kernel (the innermost pass of
- * PA_FP32_GUARD plans whose rows hold 3072 to 4608 values) waits for each bulk copy with
- * a time limit; when a wait runs out the kernel sets bit 0 of the plan's device error
- * word and returns instead of spinning. After this call, the next `launches` launches of
- * that kernel issue no copy and wait 10 microseconds on a barrier phase that nothing can
- * complete, so their wait runs out with no copy in flight. The batch's synchronising call
- * (pa_hash_batch of a PA_FP32_GUARD plan or with info, pa_hash_host, pa_batch_finish)
- * then returns PA_ETIMEOUT and clears the word; that batch's outputs are not valid, and
- * the plan stays usable. Every other call reports such an error only at the next
- * synchronising call on the plan. Returns PA_EUNSUPPORTED for plans whose innermost
- * pass does not use the pipelined kernel, PA_EINVAL for a NULL plan.
+ * the paper has no counterpart). The staged last pass (pa_plan_set_staged) waits for each
+ * of its tiled copies with a time limit;
+ * when a wait runs out the kernel sets bit 0 of the plan's device error word and returns
+ * instead of spinning. After this call, the next `launches` launches of that kernel issue
+ * no copy and wait 10 microseconds on a barrier phase that nothing can complete, so their
+ * wait runs out with no copy in flight. The batch's synchronising call (pa_hash_batch of a
+ * PA_FP32_GUARD plan or with info, pa_hash_host, pa_batch_finish) then returns PA_ETIMEOUT
+ * and clears the word; that batch's outputs are not valid, and the plan stays usable.
+ * Every other call reports such an error only at the next synchronising call on the plan.
+ * Returns PA_EUNSUPPORTED for plans whose last pass is not staged (staging off, or a plan
+ * it does not apply to), PA_EINVAL for a NULL plan.
  */
 int pa_plan_expire_waits(pa_plan_t *plan, uint32_t launches);
 
@@ -394,6 +423,17 @@ typedef struct {
 int pa_profile_enable(pa_plan_t *plan, int enable);
 /* stats: caller array of PA_NUM_KERNEL_KINDS entries; *count receives the number filled. */
 int pa_profile_read(pa_plan_t *plan, pa_kernel_stat_t *stats, int *count, int reset);
+
+/*
+ * pa_alu_peaks -- measured arithmetic peaks of the current device for the rooflines of
+ * the FP64 and exact modes (measurement support; the paper has no counterpart): the rate
+ * of independent double-precision fused multiply-adds in GFLOP/s (2 flops each), and the
+ * rate of products modulo p = 2^64 - 2^32 + 1 (64 x 64 -> 128-bit multiply and the
+ * reduction the NTT64 transform uses) in G products/s. Runs two short kernels on
+ * `stream` (a few ms), timed with CUDA events, and waits for them. Both outputs are host
+ * pointers. Returns PA_EINVAL for NULL outputs, PA_ECUDA on a CUDA error.
+ */
+int pa_alu_peaks(double *fp64_gflops, double *zp_gmul_s, pa_stream_t stream);
 
 /*
  * pa_hash_static -- the hash of one or two keys that share one seed, computed

@@ -98,6 +98,9 @@ def lib():
     L.pa_hash_batch.argtypes = [vp, vp, u32, u64, vp, u64, vp, ctypes.POINTER(BatchInfo)]
     L.pa_plan_set_guard.argtypes = [vp, ctypes.c_float]
     L.pa_plan_expire_waits.argtypes = [vp, u32]
+    L.pa_plan_set_staged.argtypes = [vp, ctypes.c_int]
+    L.pa_plan_set_storage_bits.argtypes = [vp, u32]
+    L.pa_alu_peaks.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp]
     L.pa_hash_batch_async.argtypes = [vp, vp, u32, u64, vp, u64, vp]
     L.pa_batch_finish.argtypes = [vp, ctypes.POINTER(BatchInfo)]
     L.pa_hash_host_async.argtypes = [vp, vp, u32, u64, vp, u64, vp]
@@ -225,9 +228,26 @@ def pa_plan_set_guard(plan: int, threshold: float) -> None:
     _check(lib().pa_plan_set_guard(plan, threshold), "pa_plan_set_guard")
 
 
+def pa_plan_set_staged(plan: int, on: bool = True) -> None:
+    """Run the plan's last pass as the TMA-staged persistent kernel (FP32, first pass <= 256)."""
+    _check(lib().pa_plan_set_staged(plan, int(bool(on))), "pa_plan_set_staged")
+
+
+def pa_plan_set_storage_bits(plan: int, bits: int) -> None:
+    """Storage-precision study: keep `bits` significand bits of every value stored between passes."""
+    _check(lib().pa_plan_set_storage_bits(plan, bits), "pa_plan_set_storage_bits")
+
+
 def pa_plan_expire_waits(plan: int, launches: int = 1) -> None:
     """Test hook: the next `launches` pipelined convolution launches let their bounded wait run out."""
     _check(lib().pa_plan_expire_waits(plan, launches), "pa_plan_expire_waits")
+
+
+def pa_alu_peaks(stream=None):
+    """(FP64 GFLOP/s, G modular products/s) measured on the current device."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib().pa_alu_peaks(ctypes.byref(a), ctypes.byref(b), _stream_handle(stream)), "pa_alu_peaks")
+    return a.value, b.value
 
 
 def pa_plan_shape(plan: int):

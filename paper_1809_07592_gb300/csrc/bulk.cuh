@@ -9,6 +9,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>  // CUtensorMap (the tiled copies' tensor descriptor)
 
 namespace pa {
 
@@ -40,6 +41,17 @@ __device__ __forceinline__ void bulk_load(void *dst_smem, const void *src_gmem, 
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                  ::"r"(smem_addr(dst_smem)), "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar))
                  : "memory");
+}
+
+// Tiled copy of one box of a 2-D tensor (cp.async.bulk.tensor, the TMA's tiled form) into
+// shared memory at dst (128-byte aligned), completion counted on `bar`. (x, y) is the box's
+// first element: x along the contiguous dimension, in elements; x times the element size
+// must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_2d(void *dst_smem, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_addr(dst_smem)), "l"(map), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {

@@ -472,6 +472,32 @@ __device__ __forceinline__ uint32_t bslot(uint32_t a, uint32_t col) {
     }
 }
 
+// Period of a boundary's slot map: every map above satisfies
+//     slot(x + Q) = slot(x) + slot(Q)   for all x
+// (Q = 16 / COLS for interleaved columns, 16 for a skewed row, D for a padded row,
+// 1 for the plain index), and hence slot(x + c, col) = slot(x, col) + slot(c, 0)
+// whenever x or c is a multiple of Q. Stage loops use that to compute one slot per
+// butterfly group and reach the others by compile-time offsets.
+template <typename T, int LEN, int COLS, int E, int SPAN>
+constexpr int slot_period() {
+    static_assert(COLS == 1 || 16 % COLS == 0, "interleaved columns must divide 16");
+    if constexpr (COLS > 1) {
+        return 16 / COLS;
+    } else {
+        constexpr int RC = Plan<LEN, E>::RC;
+        if constexpr (RC > 1 && SPAN % RC == 0) {
+            if constexpr (RC % 2 == 1) {
+                return SPAN == RC ? 1 : 16;
+            } else {
+                constexpr int W = 128 / (int)sizeof(cx<T>);
+                return RC / gcd_c(RC, W) * W;
+            }
+        } else {
+            return 16;
+        }
+    }
+}
+
 // One Stockham stage of radix R at span P, from registers (already loaded
 // with this stage's inputs) to shared memory. Thread tq handles the E/R
 // butterfly groups i = tq + b*TC; group i reads elements i + r*LEN/R,
@@ -480,6 +506,7 @@ __device__ __forceinline__ uint32_t bslot(uint32_t a, uint32_t col) {
 template <typename T, int LEN, int COLS, int E, int R, int P, bool INV>
 __device__ __forceinline__ void stage_to_smem(cx<T> *sm, cx<T> *v, uint32_t tq, uint32_t col, const TwTab<T> &tw) {
     constexpr int TC = LEN / E;
+    constexpr int Q = slot_period<T, LEN, COLS, E, P * R>();
 #pragma unroll
     for (int b = 0; b < E / R; ++b) {
         const uint32_t i = tq + (uint32_t)b * TC;
@@ -487,8 +514,15 @@ __device__ __forceinline__ void stage_to_smem(cx<T> *sm, cx<T> *v, uint32_t tq, 
         if (P > 1) stage_twiddles<T, INV, R>(v + b * R, tw, k * (tw.F / (R * P)));
         dft<T, R, INV>(v + b * R);
         const uint32_t base = (i - k) * R + k;
+        if constexpr (P % Q == 0 || (P == 1 && R % Q == 0)) {
+            // offsets r*P are multiples of Q, or (P = 1, so k = 0) base = i*R is one
+            const uint32_t s0 = bslot<T, LEN, COLS, E, P * R>(base, col);
 #pragma unroll
-        for (int r = 0; r < R; ++r) sm[bslot<T, LEN, COLS, E, P * R>(base + (uint32_t)r * P, col)] = v[b * R + r];
+            for (int r = 0; r < R; ++r) sm[s0 + bslot<T, LEN, COLS, E, P * R>((uint32_t)(r * P), 0)] = v[b * R + r];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) sm[bslot<T, LEN, COLS, E, P * R>(base + (uint32_t)r * P, col)] = v[b * R + r];
+        }
     }
 }
 
@@ -497,11 +531,18 @@ __device__ __forceinline__ void stage_to_smem(cx<T> *sm, cx<T> *v, uint32_t tq, 
 template <typename T, int LEN, int COLS, int E, int R, int SPAN>
 __device__ __forceinline__ void load_from_smem(const cx<T> *sm, cx<T> *v, uint32_t tq, uint32_t col) {
     constexpr int TC = LEN / E;
+    constexpr int Q = slot_period<T, LEN, COLS, E, SPAN>();
 #pragma unroll
     for (int b = 0; b < E / R; ++b) {
         const uint32_t i = tq + (uint32_t)b * TC;
+        if constexpr ((LEN / R) % Q == 0) {  // offsets r*LEN/R are multiples of Q
+            const uint32_t s0 = bslot<T, LEN, COLS, E, SPAN>(i, col);
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[b * R + r] = sm[bslot<T, LEN, COLS, E, SPAN>(i + (uint32_t)r * (LEN / R), col)];
+            for (int r = 0; r < R; ++r) v[b * R + r] = sm[s0 + bslot<T, LEN, COLS, E, SPAN>((uint32_t)(r * (LEN / R)), 0)];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[b * R + r] = sm[bslot<T, LEN, COLS, E, SPAN>(i + (uint32_t)r * (LEN / R), col)];
+        }
     }
 }
 
@@ -578,9 +619,11 @@ __device__ __forceinline__ void cta_fft(cx<T> *sm, cx<T> *v, uint32_t tq, uint32
 
 // Forward transform of a contiguous row of LEN = RO * 2^k elements (RO > 1).
 // The first stage has the odd (or composite) radix RC = Plan::RC at span 1: group
-// g < LEN / RC reads elements g + r LEN / RC through ld(index), transforms, and
-// writes shared-memory slots g RC + r (odd_first_stage). The power-of-two stages
-// follow (fwd_odd_rest); outputs end in registers (idx_e).
+// g = tq + j TC < LEN / RC reads elements g + r LEN / RC through ld(offset), the offset
+// j TC + r LEN / RC counted from element tq (a compile-time constant, so the caller's
+// base pointer for thread tq takes immediate offsets), transforms, and writes
+// shared-memory slots g RC + r (odd_first_stage). The power-of-two stages follow
+// (fwd_odd_rest); outputs end in registers (idx_e).
 template <typename T, int LEN, int E, class Ld>
 __device__ __forceinline__ void odd_first_stage(cx<T> *sm, uint32_t tq, Ld ld) {
     using PL = Plan<LEN, E>;
@@ -592,7 +635,7 @@ __device__ __forceinline__ void odd_first_stage(cx<T> *sm, uint32_t tq, Ld ld) {
         if (g < (uint32_t)K) {
             cx<T> u[RC];
 #pragma unroll
-            for (int r = 0; r < RC; ++r) u[r] = ld(g + (uint32_t)r * K);
+            for (int r = 0; r < RC; ++r) u[r] = ld((uint32_t)(j * TC + r * K));
             dft_comp<T, PL::RO, PL::R0C, false>(u);
 #pragma unroll
             for (int r = 0; r < RC; ++r) sm[ridx<T, LEN, E, RC>(g * RC + (uint32_t)r)] = u[r];
@@ -614,8 +657,9 @@ __device__ __forceinline__ void cta_fft_fwd_odd(cx<T> *sm, cx<T> *v, uint32_t tq
 
 // Inverse transform of a row (RO > 1): power-of-two stages from registers
 // (idx_e layout) into shared memory, then the odd (or composite) last stage at
-// span K = LEN / RC: group g < K reads slots g + r K, takes the twiddles
-// w_LEN^{-r g}, transforms, and its outputs go through st(g + r K, value).
+// span K = LEN / RC: group g = tq + j TC < K reads slots g + r K, takes the twiddles
+// w_LEN^{-r g}, transforms, and its output g + r K goes through st(j TC + r K, value)
+// (offset from element tq, as for ld above).
 template <typename T, int LEN, int E, class St>
 __device__ __forceinline__ void cta_fft_inv_odd(cx<T> *sm, cx<T> *v, uint32_t tq, const TwTab<T> &tw, St st) {
     using PL = Plan<LEN, E>;
@@ -628,12 +672,18 @@ __device__ __forceinline__ void cta_fft_inv_odd(cx<T> *sm, cx<T> *v, uint32_t tq
         const uint32_t g = tq + (uint32_t)j * TC;
         if (g < (uint32_t)K) {
             cx<T> u[RC];
+            if constexpr (K % slot_period<T, LEN, 1, E, K>() == 0) {  // offsets r*K are multiples of the period
+                const uint32_t s0 = ridx<T, LEN, E, K>(g);
 #pragma unroll
-            for (int r = 0; r < RC; ++r) u[r] = sm[ridx<T, LEN, E, K>(g + (uint32_t)r * K)];
+                for (int r = 0; r < RC; ++r) u[r] = sm[s0 + ridx<T, LEN, E, K>((uint32_t)(r * K))];
+            } else {
+#pragma unroll
+                for (int r = 0; r < RC; ++r) u[r] = sm[ridx<T, LEN, E, K>(g + (uint32_t)r * K)];
+            }
             stage_twiddles<T, true, RC>(u, tw, g * (tw.F / LEN));
             dft_comp<T, PL::RO, PL::R0C, true>(u);
 #pragma unroll
-            for (int r = 0; r < RC; ++r) st(g + (uint32_t)r * K, u[r]);
+            for (int r = 0; r < RC; ++r) st((uint32_t)(j * TC + r * K), u[r]);
         }
     }
 }

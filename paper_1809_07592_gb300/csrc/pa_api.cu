@@ -101,8 +101,11 @@ struct pa_plan {
     uint32_t max_chunk_pairs = 1;
     uint32_t *popc = nullptr;    // per key
     uint32_t *marg = nullptr;    // per key, float bits
-    uint32_t *err = nullptr;     // device word: bit 0 = a bounded copy wait ran out of time
-    uint32_t expire_launches = 0;  // test hook: pipelined launches left whose first wait is made to run out
+    uint32_t *err = nullptr;     // device words: [0] error bits (bit 0: a bounded copy wait ran out of
+                                 // time), [1] and [2] the staged inverse pass's tile ticket and exit count
+    bool staged = false;           // last pass as the TMA-staged persistent kernel (pa_plan_set_staged)
+    uint32_t store_bits = 0;       // storage-precision study: significand bits kept between passes (0: all)
+    uint32_t expire_launches = 0;  // test hook: staged launches left whose first wait is made to run out
     uint32_t key_cap = 0;
     float *h_marg = nullptr;     // pinned: h_cap margins, then the error word
     uint32_t h_cap = 0;
@@ -360,6 +363,16 @@ uint32_t chunk_pairs_limit(const pa_plan_t *p) {
     return (uint32_t)lim;
 }
 
+// Storage-precision study (pa_plan_set_storage_bits): round `pairs` slots of values a pass
+// has just stored to the plan's significand width. Only FP32 plans carry the setting.
+template <typename T>
+cudaError_t round_stored(const pa_plan_t *p, cx<T> *slots, uint32_t pairs, cudaStream_t st) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (p->store_bits) return launch_round_significand(reinterpret_cast<float *>(slots), 2ull * pairs * p->L, p->store_bits, st);
+    }
+    return cudaSuccess;
+}
+
 template <typename T>
 int run_seed(pa_plan_t *p, const uint64_t *seed, cudaStream_t st) {
     const TwTab<T> tw = tw_of<T>(p);
@@ -372,6 +385,7 @@ int run_seed(pa_plan_t *p, const uint64_t *seed, cudaStream_t st) {
         PA_CUDA(launch_mid<T>(g.lgM, false, W, p->L, g.inner(), 1, tw, st));
     }
     { Timed t_(p, K_MIDDLE_SPEC, st); PA_CUDA(launch_middle<T>(g.ro, g.lgI, 1, W, spec, p->L, 1, tw, inv_length<T>(p->L), st)); }
+    PA_CUDA(round_stored<T>(p, spec, 1, st));
     return PA_OK;
 }
 
@@ -418,9 +432,9 @@ int run_keys_real(pa_plan_t *p, const uint64_t *keys, uint32_t nkeys, uint64_t k
     return PA_OK;
 }
 
-// Wait limit handed to the next pipelined convolution launch: 0 (the kernel's own 1 s
-// limit, copies issued as usual), or, while the test hook of pa_plan_expire_waits is
-// armed, 10 us on a barrier phase that no copy completes.
+// Wait limit handed to the next launch of the TMA-staged inverse pass: 0 (the kernel's
+// own 1 s limit, copies issued as usual), or, while the test hook of
+// pa_plan_expire_waits is armed, 10 us on a barrier phase that no copy completes.
 uint32_t take_expire(pa_plan_t *p) {
     if (p->expire_launches == 0) return 0u;
     --p->expire_launches;
@@ -433,7 +447,7 @@ int run_keys(pa_plan_t *p, const uint64_t *keys, uint32_t nkeys, uint64_t kstrid
     if constexpr (!std::is_same<T, Zp>::value) {
         // A lone key (alone, or the last of an odd batch) takes the half-length form; key
         // pairs stay in the pair form (measured 28 % faster per key than the half-length form).
-        if (p->real && p->real->seeded && (nkeys & 1)) {
+        if (p->real && p->real->seeded && (nkeys & 1) && p->store_bits == 0) {
             if (nkeys > 1) {
                 const int rc = run_keys<T>(p, keys, nkeys - 1, kstride, out, ostride, popc, marg, st);
                 if (rc != PA_OK) return rc;
@@ -456,15 +470,19 @@ int run_keys(pa_plan_t *p, const uint64_t *keys, uint32_t nkeys, uint64_t kstrid
         const uint64_t *kp = keys + (uint64_t)k0 * kstride;
         uint64_t *op = out + (uint64_t)k0 * ostride;
         { Timed t_(p, K_FWD_KEYS, st); PA_CUDA(launch_fwd_keys<T>(g.lg1, kp, nk, kstride, p->n, W, p->L, pairs, tw, popc + k0, st, p->koff)); }
+        PA_CUDA(round_stored<T>(p, W, pairs, st));
         if (g.lgM) {
             { Timed t_(p, K_MID_FWD, st); PA_CUDA(launch_mid<T>(g.lgM, false, W, p->L, g.inner(), pairs, tw, st)); }
-            { Timed t_(p, K_MIDDLE_CONV, st); PA_CUDA(launch_middle<T>(g.ro, g.lgI, 0, W, spec, p->L, pairs, tw, one<T>(), st, p->err, take_expire(p))); }
+            PA_CUDA(round_stored<T>(p, W, pairs, st));
+            { Timed t_(p, K_MIDDLE_CONV, st); PA_CUDA(launch_middle<T>(g.ro, g.lgI, 0, W, spec, p->L, pairs, tw, one<T>(), st)); }
+            PA_CUDA(round_stored<T>(p, W, pairs, st));
             { Timed t_(p, K_MID_INV, st); PA_CUDA(launch_mid<T>(g.lgM, true, W, p->L, g.inner(), pairs, tw, st)); }
         } else {
             Timed t_(p, K_MIDDLE_CONV, st);
-            PA_CUDA(launch_middle<T>(g.ro, g.lgI, 0, W, spec, p->L, pairs, tw, one<T>(), st, p->err, take_expire(p)));
+            PA_CUDA(launch_middle<T>(g.ro, g.lgI, 0, W, spec, p->L, pairs, tw, one<T>(), st));
         }
-        { Timed t_(p, K_INV_BITS, st); PA_CUDA(launch_inv_bits<T>(g.lg1, W, p->L, p->m, nk, popc + k0, marg + k0, op, ostride, pairs, tw, st, p->modified ? kp : nullptr, kstride)); }
+        PA_CUDA(round_stored<T>(p, W, pairs, st));
+        { Timed t_(p, K_INV_BITS, st); PA_CUDA(launch_inv_bits<T>(g.lg1, W, p->L, p->m, nk, popc + k0, marg + k0, op, ostride, pairs, tw, st, p->modified ? kp : nullptr, kstride, false, p->staged ? p->err : nullptr, take_expire(p))); }
     }
     return PA_OK;
 }
@@ -774,8 +792,9 @@ int plan_create(uint64_t n, uint64_t m, pa_dtype_t dtype, const Geometry *force,
     p->L = geo.L;
     p->geo = geo;
     cudaError_t e = cudaMalloc(&p->spec, (size_t)p->L * elem_bytes(dtype));
-    if (e == cudaSuccess) e = cudaMalloc(&p->err, sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMemset(p->err, 0, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&p->err, 4 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(p->err, 0, 4 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);  // zero before any stream of the plan uses them
     if (e != cudaSuccess) {
         free_plan(p);
         if (e == cudaErrorMemoryAllocation) {
@@ -996,10 +1015,27 @@ int pa_plan_set_guard(pa_plan_t *p, float threshold) {
     return PA_OK;
 }
 
+int pa_plan_set_staged(pa_plan_t *p, int on) {
+    if (!p) return PA_EINVAL;
+    std::lock_guard<std::mutex> lk(p->mu);
+    p->staged = on != 0;
+    return PA_OK;
+}
+
+int pa_plan_set_storage_bits(pa_plan_t *p, uint32_t bits) {
+    if (!p || bits > 23) return PA_EINVAL;
+    if (p->dtype != PA_FP32_GUARD) return PA_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lk(p->mu);
+    p->store_bits = (bits == 23) ? 0u : bits;
+    p->seeded = false;  // the cached spectrum was stored at the old width: pa_set_seed again
+    return PA_OK;
+}
+
 int pa_plan_expire_waits(pa_plan_t *p, uint32_t launches) {
     if (!p) return PA_EINVAL;
     const Geometry &g = p->geo;
-    if (p->dtype != PA_FP32_GUARD || !pipe_fits(g.inner(), elem_bytes(p->dtype))) return PA_EUNSUPPORTED;
+    if (!p->staged || p->dtype != PA_FP32_GUARD || !inv_bits_staged(elem_bytes(p->dtype), g.lg1))
+        return PA_EUNSUPPORTED;
     std::lock_guard<std::mutex> lk(p->mu);
     p->expire_launches = launches;
     return PA_OK;
@@ -1151,7 +1187,11 @@ int pa_batch_finish(pa_plan_t *p, pa_batch_info_t *info) {
     std::memcpy(&err_word, p->h_marg + b.nkeys, sizeof(uint32_t));
     if (err_word != 0) {
         PA_CUDA(cudaMemset(p->err, 0, sizeof(uint32_t)));
-        return PA_ETIMEOUT;  // a bounded device wait ran out: this batch's outputs are not valid
+        // this batch's outputs are not valid: bit 0, a bounded device wait ran out; bit 1, a
+        // staging buffer was not aligned for its tiled copy (the kernel copied nothing)
+        if (err_word & 1u) return PA_ETIMEOUT;
+        g_last_cuda_error = "device staging buffer misaligned for its tiled copy";
+        return PA_ECUDA;
     }
     if (info) info->escalated = 0;
     uint32_t escalated = 0;

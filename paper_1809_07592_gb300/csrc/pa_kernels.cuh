@@ -119,6 +119,32 @@ __device__ __forceinline__ uint32_t *key_stage(unsigned char *smem_raw) {
 template <typename T, int LEN, int COLS>
 constexpr size_t stage_bytes() { return (size_t)LEN * sizeof(uint32_t); }
 
+// Two per-thread counters reduced over the CTA (sum, or max when MAX): warp reductions,
+// then warp 0 over the warps' partial results (kept in scratch, 64 words of shared
+// memory). The totals are valid in thread 0. Every thread of the CTA must call it (it
+// holds a barrier). The per-key counters of a batch (key popcounts, rounding margins)
+// are accumulated with one atomic per key and CTA this way: one atomic per warp on the
+// same few words from thousands of CTAs at once queues up in the memory system and
+// measurably slows the whole pass.
+template <bool MAX>
+__device__ __forceinline__ void cta_reduce2(uint32_t &a, uint32_t &b, uint32_t *scratch) {
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    a = MAX ? __reduce_max_sync(0xffffffffu, a) : __reduce_add_sync(0xffffffffu, a);
+    b = MAX ? __reduce_max_sync(0xffffffffu, b) : __reduce_add_sync(0xffffffffu, b);
+    if (lane == 0) {
+        scratch[warp] = a;
+        scratch[32 + warp] = b;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t nw = blockDim.x >> 5;
+        a = lane < nw ? scratch[lane] : 0u;
+        b = lane < nw ? scratch[32 + lane] : 0u;
+        a = MAX ? __reduce_max_sync(0xffffffffu, a) : __reduce_add_sync(0xffffffffu, a);
+        b = MAX ? __reduce_max_sync(0xffffffffu, b) : __reduce_add_sync(0xffffffffu, b);
+    }
+}
+
 // Single keys in half-length transforms: transform element t carries key bits 2t
 // (real part) and 2t+1 (imaginary part). even_bits gathers the even-position bits of
 // x into the low 16 bits; spread_bits is its inverse (low 16 bits to even positions).
@@ -205,9 +231,9 @@ __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
         ca += __popc(wa);
         cb += __popc(wb);
     }
-    ca = __reduce_add_sync(0xffffffffu, ca);
-    cb = __reduce_add_sync(0xffffffffu, cb);
-    if ((threadIdx.x & 31) == 0 && (ca | cb)) {
+    __shared__ uint32_t red[64];
+    cta_reduce2<false>(ca, cb, red);  // also publishes the staged rows
+    if (threadIdx.x == 0 && (ca | cb)) {
         if (PACK) {
             atomicAdd(popc + pair, ca + cb);
         } else {
@@ -215,7 +241,6 @@ __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
             if (cb) atomicAdd(popc + 2 * pair + 1, cb);
         }
     }
-    __syncthreads();
     cx<T> v[E];
 #pragma unroll
     for (int s = 0; s < E; ++s) {
@@ -313,143 +338,31 @@ __global__ void __launch_bounds__(LEN / E, min_blocks_inner(LEN / E, sizeof(cx<T
     cx<T> *sm = reinterpret_cast<cx<T> *>(smem_raw);
     const uint32_t tq = threadIdx.x;
     const uint64_t row = blockIdx.x, pair = blockIdx.y;
-    cx<T> *w = W + pair * L + row * LEN;
-    cx<T> *sp = spec + row * LEN;
+    // thread tq's elements sit at compile-time offsets from element tq of the row
+    cx<T> *wt = W + pair * L + row * LEN + tq;
+    cx<T> *spt = spec + row * LEN + tq;
     cx<T> v[E];
     if constexpr (Plan<LEN, E>::RO == 1) {
 #pragma unroll
-        for (int s = 0; s < E; ++s) v[s] = w[idx_r0<LEN, E>(tq, s)];
+        for (int s = 0; s < E; ++s) v[s] = wt[idx_r0<LEN, E>(0, s)];
         cta_fft<T, LEN, 1, E, false>(sm, v, tq, 0, tw);
     } else {
-        cta_fft_fwd_odd<T, LEN, E>(sm, v, tq, tw, [&](uint32_t i) { return w[i]; });
+        cta_fft_fwd_odd<T, LEN, E>(sm, v, tq, tw, [&](uint32_t o) { return wt[o]; });
     }
     if (MODE == 1) {
 #pragma unroll
-        for (int s = 0; s < E; ++s) sp[idx_e<LEN, E>(tq, s)] = Arith<T>::mul(v[s], scale);
+        for (int s = 0; s < E; ++s) spt[idx_e<LEN, E>(0, s)] = Arith<T>::mul(v[s], scale);
         return;
     }
 #pragma unroll
-    for (int s = 0; s < E; ++s) v[s] = Arith<T>::mul(v[s], sp[idx_e<LEN, E>(tq, s)]);
+    for (int s = 0; s < E; ++s) v[s] = Arith<T>::mul(v[s], spt[idx_e<LEN, E>(0, s)]);
     __syncthreads();  // the forward transform's last shared-memory reads are done
     if constexpr (Plan<LEN, E>::RO == 1) {
         cta_fft<T, LEN, 1, E, true>(sm, v, tq, 0, tw);
 #pragma unroll
-        for (int s = 0; s < E; ++s) w[idx_r0<LEN, E>(tq, s)] = v[s];
+        for (int s = 0; s < E; ++s) wt[idx_r0<LEN, E>(0, s)] = v[s];
     } else {
-        cta_fft_inv_odd<T, LEN, E>(sm, v, tq, tw, [&](uint32_t i, cx<T> x) { w[i] = x; });
-    }
-}
-
-// The fused convolution step (MODE 0 of k_middle) as a persistent, pipelined
-// kernel: each CTA owns a contiguous run of tiles (tile t = row t / pairs of
-// pair t % pairs, so consecutive tiles share a seed-spectrum row) and keeps two
-// staging rows in shared memory, filled by bulk asynchronous copies: the input
-// row of the next tile is copied while the current tile is transformed, and the
-// seed-spectrum row is copied only when the row changes. The arithmetic is
-// k_middle's, step for step. A copy wait that runs out of time sets bit 0 of
-// *err and the CTA returns (after a bounded wait for its copies in flight).
-// expire_ns != 0 is a test hook for that error path: the CTA issues no copy at
-// all and waits expire_ns on a barrier phase that nothing can complete, so the
-// wait runs out with no copy in flight, sets the error bit and returns.
-template <typename T, int LEN, int E>
-__global__ void __launch_bounds__(LEN / E, min_blocks_inner(LEN / E, sizeof(cx<T>)))
-    k_middle_pipe(cx<T> *__restrict__ W, const cx<T> *__restrict__ spec, uint64_t L, uint32_t pairs,
-                  uint32_t tiles_per_cta, TwTab<T> tw, uint32_t *__restrict__ err, uint32_t expire_ns) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    constexpr uint32_t kRowBytes = LEN * sizeof(cx<T>);
-    static_assert(kRowBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
-    cx<T> *stg = reinterpret_cast<cx<T> *>(smem_raw);  // staged input row
-    cx<T> *ssp = stg + LEN;                              // staged seed-spectrum row
-    cx<T> *sm = ssp + LEN;                               // exchange buffer of the transform
-    __shared__ __align__(8) uint64_t bar[2];             // [0]: input row, [1]: spectrum row
-    const uint32_t tq = threadIdx.x;
-    const uint32_t ntiles = (uint32_t)(L / LEN) * pairs;
-    const uint32_t t0 = blockIdx.x * tiles_per_cta;
-    const uint32_t t1 = (t0 + tiles_per_cta < ntiles) ? t0 + tiles_per_cta : ntiles;
-    if (t0 >= t1) return;
-    auto row_of = [&](uint32_t t) { return W + (uint64_t)(t % pairs) * L + (uint64_t)(t / pairs) * LEN; };
-    uint32_t srow = t0 / pairs;  // spectrum row staged (or in flight) in ssp
-    if (tq == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        mbar_init_fence();
-        if (expire_ns == 0) {
-            mbar_arrive_expect_tx(&bar[0], kRowBytes);
-            bulk_load(stg, row_of(t0), kRowBytes, &bar[0]);
-            mbar_arrive_expect_tx(&bar[1], kRowBytes);
-            bulk_load(ssp, spec + (uint64_t)srow * LEN, kRowBytes, &bar[1]);
-        }
-    }
-    __syncthreads();
-    if (expire_ns != 0) {  // test hook: phase 0 of bar[0] has no arrival and no copy, so it never completes
-        if (tq == 0 && !mbar_wait(&bar[0], 0, expire_ns)) atomicOr(err, 1u);
-        return;
-    }
-    uint32_t pd = 0, ps = 0;
-    bool spec_wait = true;
-    for (uint32_t t = t0; t < t1; ++t) {
-        const uint32_t row = t / pairs;
-        if (row != srow) {
-            // every thread finished reading ssp before the barrier that closed the last tile
-            if (tq == 0) {
-                mbar_arrive_expect_tx(&bar[1], kRowBytes);
-                bulk_load(ssp, spec + (uint64_t)row * LEN, kRowBytes, &bar[1]);
-            }
-            srow = row;
-            spec_wait = true;
-        }
-        bool ok = mbar_wait(&bar[0], pd);
-        pd ^= 1u;
-        if (!__syncthreads_and(ok)) {
-            if (tq == 0) {  // record the failure, then give the copies in flight a bounded wait
-                atomicOr(err, 1u);
-                mbar_wait(&bar[0], pd ^ 1u);
-                if (spec_wait) mbar_wait(&bar[1], ps);
-            }
-            return;
-        }
-        cx<T> v[E];
-        if constexpr (Plan<LEN, E>::RO == 1) {
-#pragma unroll
-            for (int s = 0; s < E; ++s) v[s] = stg[idx_r0<LEN, E>(tq, s)];
-        } else {
-            odd_first_stage<T, LEN, E>(sm, tq, [&](uint32_t i) { return stg[i]; });
-        }
-        __syncthreads();  // stg has been read: refill it with the next tile's row
-        if (tq == 0 && t + 1 < t1) {
-            mbar_arrive_expect_tx(&bar[0], kRowBytes);
-            bulk_load(stg, row_of(t + 1), kRowBytes, &bar[0]);
-        }
-        if constexpr (Plan<LEN, E>::RO == 1) {
-            cta_fft<T, LEN, 1, E, false>(sm, v, tq, 0, tw);
-        } else {
-            fwd_odd_rest<T, LEN, E>(sm, v, tq, tw);
-        }
-        if (spec_wait) {
-            ok = mbar_wait(&bar[1], ps);
-            ps ^= 1u;
-            spec_wait = false;
-            if (!__syncthreads_and(ok)) {
-                if (tq == 0) {
-                    atomicOr(err, 1u);
-                    mbar_wait(&bar[1], ps ^ 1u);
-                    if (t + 1 < t1) mbar_wait(&bar[0], pd);
-                }
-                return;
-            }
-        }
-#pragma unroll
-        for (int s = 0; s < E; ++s) v[s] = Arith<T>::mul(v[s], ssp[idx_e<LEN, E>(tq, s)]);
-        __syncthreads();  // the forward transform's last shared-memory reads are done
-        cx<T> *w = row_of(t);
-        if constexpr (Plan<LEN, E>::RO == 1) {
-            cta_fft<T, LEN, 1, E, true>(sm, v, tq, 0, tw);
-#pragma unroll
-            for (int s = 0; s < E; ++s) w[idx_r0<LEN, E>(tq, s)] = v[s];
-        } else {
-            cta_fft_inv_odd<T, LEN, E>(sm, v, tq, tw, [&](uint32_t i, cx<T> x) { w[i] = x; });
-        }
-        __syncthreads();  // sm and ssp are free for the next tile
+        cta_fft_inv_odd<T, LEN, E>(sm, v, tq, tw, [&](uint32_t o, cx<T> x) { wt[o] = x; });
     }
 }
 
@@ -461,6 +374,56 @@ template <> struct BitsWord<32> { using type = uint32_t; };
 
 __device__ __forceinline__ float margin_to_float(float x) { return x; }
 __device__ __forceinline__ float margin_to_float(double x) { return __double2float_ru(x); }
+
+// Round, mod 2 and pack the outputs of the level-1 inverse transform of one column
+// (pair form): v holds rows t1 = idx_r0(tq, s) of column u = u0 + col, the real part
+// belonging to key ka, the imaginary part to key kb (if has_b). Output bit i = t1*S + u
+// of a key is element i of the convolution window; bits >= m are written 0. Each key's
+// rounding margin max |w - rint(w)| over its m outputs goes to margin_bits (float bits,
+// atomicMax; margins are >= 0, so integer order is float order). With xkeys, the bits
+// are XORed with key bits 0 .. m-1 (the identity block of the modified hash, Eq. 3).
+template <typename T, int LEN, int COLS, int E>
+__device__ __forceinline__ void pack_pair_bits(const cx<T> *v, uint32_t tq, uint32_t col, uint64_t S, uint64_t u0,
+                                               uint64_t m, uint32_t popa, uint32_t popb, uint32_t ka, uint32_t kb,
+                                               bool has_b, typename BitsWord<COLS>::type *oa,
+                                               typename BitsWord<COLS>::type *ob, uint32_t *margin_bits,
+                                               const uint64_t *xkeys, uint64_t xstride) {
+    using word_t = typename BitsWord<COLS>::type;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t u = u0 + col;
+    const uint64_t nchunks = ((m + 63) >> 6) * (64 / COLS);
+    typename Enc<T>::M ma = 0, mb = 0;
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+        const uint64_t t1 = idx_r0<LEN, E>(tq, s);
+        const uint64_t i = t1 * S + u;
+        const uint64_t ci = (t1 * S + u0) / COLS;  // output chunk of this row's COLS bits
+        // rows past the last output word are not decoded (warp-uniform test: the ballot needs every lane)
+        if (!__any_sync(0xffffffffu, ci < nchunks)) continue;
+        bool bit_a, bit_b;
+        Enc<T>::decode(v[s], popa, popb, i < m, bit_a, bit_b, ma, mb);
+        const uint32_t ba = __ballot_sync(0xffffffffu, bit_a);
+        const uint32_t bb = __ballot_sync(0xffffffffu, bit_b);
+        if (col == 0 && ci < nchunks) {
+            const uint32_t sh = lane;  // lane = group * COLS
+            const uint32_t msk = (COLS == 32) ? 0xffffffffu : ((1u << COLS) - 1u);
+            uint32_t ya = (ba >> sh) & msk, yb = (bb >> sh) & msk;
+            if (xkeys) {  // modified Toeplitz hash (Eq. 3): the identity block adds key bits 0 .. m-1
+                ya ^= aligned_bits<COLS>(xkeys + (uint64_t)ka * xstride, m, ci * COLS);
+                if (has_b) yb ^= aligned_bits<COLS>(xkeys + (uint64_t)kb * xstride, m, ci * COLS);
+            }
+            oa[ci] = (word_t)ya;
+            if (has_b) ob[ci] = (word_t)yb;
+        }
+    }
+    uint32_t fa = __float_as_uint(margin_to_float(ma)), fb = __float_as_uint(margin_to_float(mb));
+    __shared__ uint32_t red[64];
+    cta_reduce2<true>(fa, fb, red);
+    if (threadIdx.x == 0) {
+        atomicMax(margin_bits + ka, fa);
+        if (has_b) atomicMax(margin_bits + kb, fb);
+    }
+}
 
 // Level-1 inverse pass with the post-processing step of the paper's Fig. 2 (the
 // inverse transform's output rounded to integers, then reduced mod 2): round, mod 2, pack.
@@ -496,9 +459,8 @@ __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
     const uint32_t popb = PACK ? popa : (has_b ? popc[kb] : 0u);
     word_t *oa = reinterpret_cast<word_t *>(out + (uint64_t)ka * ostride);
     word_t *ob = reinterpret_cast<word_t *>(out + (uint64_t)kb * ostride);
-    const uint64_t nchunks = ((m + 63) >> 6) * (64 / COLS);
-    typename Enc<T>::M ma = 0, mb = 0;
     if constexpr (PACK) {
+        typename Enc<T>::M ma = 0, mb = 0;
         // chunk ci: the row's COLS elements t = t1*S + u0 + c, i.e. output bits 2*(t1*S + u0) .. +2*COLS
         using word2_t = typename BitsWord<2 * COLS>::type;
         word2_t *o2 = reinterpret_cast<word2_t *>(out + (uint64_t)ka * ostride);
@@ -520,40 +482,113 @@ __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
                 o2[ci] = (word2_t)y;
             }
         }
-        uint32_t f = __float_as_uint(margin_to_float(ma > mb ? ma : mb));
-        f = __reduce_max_sync(0xffffffffu, f);
-        if (lane == 0) atomicMax(margin_bits + ka, f);
+        uint32_t f = __float_as_uint(margin_to_float(ma > mb ? ma : mb)), unused = 0u;
+        __shared__ uint32_t red[64];
+        cta_reduce2<true>(f, unused, red);
+        if (threadIdx.x == 0) atomicMax(margin_bits + ka, f);
         return;
     }
-#pragma unroll
-    for (int s = 0; s < E; ++s) {
-        const uint64_t t1 = idx_r0<LEN, E>(tq, s);
-        const uint64_t i = t1 * S + u;
-        const uint64_t ci = (t1 * S + u0) / COLS;  // output chunk of this row's COLS bits
-        // rows past the last output word are not decoded (warp-uniform test: the ballot needs every lane)
-        if (!__any_sync(0xffffffffu, ci < nchunks)) continue;
-        bool bit_a, bit_b;
-        Enc<T>::decode(v[s], popa, popb, i < m, bit_a, bit_b, ma, mb);
-        const uint32_t ba = __ballot_sync(0xffffffffu, bit_a);
-        const uint32_t bb = __ballot_sync(0xffffffffu, bit_b);
-        if (col == 0 && ci < nchunks) {
-            const uint32_t sh = lane;  // lane = group * COLS
-            const uint32_t msk = (COLS == 32) ? 0xffffffffu : ((1u << COLS) - 1u);
-            uint32_t ya = (ba >> sh) & msk, yb = (bb >> sh) & msk;
-            if (xkeys) {  // modified Toeplitz hash (Eq. 3): the identity block adds key bits 0 .. m-1
-                ya ^= aligned_bits<COLS>(xkeys + (uint64_t)ka * xstride, m, ci * COLS);
-                if (has_b) yb ^= aligned_bits<COLS>(xkeys + (uint64_t)kb * xstride, m, ci * COLS);
+    pack_pair_bits<T, LEN, COLS, E>(v, tq, col, S, u0, m, popa, popb, ka, kb, has_b, oa, ob, margin_bits, xkeys, xstride);
+}
+
+// The level-1 inverse pass of key pairs (FP32, pair form) as a persistent kernel whose
+// input tiles are staged by the TMA: tile t is the COLS x LEN block of columns
+// u0 .. u0+COLS-1 of pair t / (S / COLS), copied by one tiled copy into shared memory.
+// The copy of a CTA's next tile is issued as soon as every thread has read the current
+// one, so a copy is in flight while the tile is transformed and decoded: the pass keeps
+// enough bytes in flight without spending registers on them. The arithmetic is
+// k_inv_bits's, step for step. The tensor map describes the work buffer as a
+// (pairs * LEN) x S array of 8-byte elements (row a of pair p at row p*LEN + a).
+//
+// Tiles are handed out by a ticket counter (ctl[1]), so a CTA that starts late, behind
+// another stream's kernel, just takes fewer tiles. Every CTA counts itself out on ctl[2]
+// when it leaves; the last one resets both counters for the next launch (launches that
+// share ctl run in stream order). A copy wait that runs out of time sets bit 0 of ctl[0]
+// and the CTA leaves after a second bounded wait for that copy. expire_ns != 0 is a test
+// hook for that path: no CTA takes a tile or issues a copy, and each waits expire_ns on a
+// barrier phase that nothing can complete.
+template <int LEN>
+__global__ void __launch_bounds__(LEN, 768 / LEN)
+    k_inv_bits_tma(const __grid_constant__ CUtensorMap wmap, uint64_t L, uint64_t m, uint32_t nkeys, uint32_t pairs,
+                   const uint32_t *__restrict__ popc, uint32_t *__restrict__ margin_bits, uint64_t *__restrict__ out,
+                   uint64_t ostride, TwTab<float> tw, const uint64_t *__restrict__ xkeys, uint64_t xstride,
+                   uint32_t *__restrict__ ctl, uint32_t expire_ns) {
+    using T = float;
+    constexpr int E = 16, COLS = 16;
+    static_assert(LEN <= 256 && LEN >= 64, "one tiled copy moves at most 256 rows");
+    constexpr uint32_t kTileBytes = LEN * COLS * sizeof(cx<T>);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // a tiled copy's destination must be 128-byte aligned: the launch adds 128 bytes to round up
+    unsigned char *base = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+    cx<T> *stg = reinterpret_cast<cx<T> *>(base);  // staged tile: row a at stg[a * COLS .. +COLS)
+    cx<T> *sm = stg + LEN * COLS;                   // exchange buffer of the transform
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t next_tile;
+    using word_t = typename BitsWord<COLS>::type;
+    const uint32_t col = threadIdx.x % COLS, tq = threadIdx.x / COLS;
+    const uint64_t S = L >> ilog2(LEN);
+    const uint32_t ncolt = (uint32_t)(S / COLS);
+    const uint32_t ntiles = ncolt * pairs;
+    const bool aligned = (smem_addr(stg) & 127u) == 0;  // always, given the spare bytes: never copy misaligned
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_init_fence();
+        uint32_t t = ntiles;
+        if (!aligned) {
+            atomicOr(ctl, 2u);
+        } else if (expire_ns == 0) {
+            t = atomicAdd(ctl + 1, 1u);
+            if (t < ntiles) {
+                mbar_arrive_expect_tx(&bar, kTileBytes);
+                tma_load_2d(stg, &wmap, (int)((t % ncolt) * COLS), (int)((t / ncolt) * LEN), &bar);
             }
-            oa[ci] = (word_t)ya;
-            if (has_b) ob[ci] = (word_t)yb;
+        } else if (!mbar_wait(&bar, 0, expire_ns)) {  // test hook: phase 0 never completes
+            atomicOr(ctl, 1u);
         }
+        next_tile = t;
     }
-    uint32_t fa = __float_as_uint(margin_to_float(ma)), fb = __float_as_uint(margin_to_float(mb));
-    fa = __reduce_max_sync(0xffffffffu, fa);
-    fb = __reduce_max_sync(0xffffffffu, fb);
-    if (lane == 0) {
-        atomicMax(margin_bits + ka, fa);
-        if (has_b) atomicMax(margin_bits + kb, fb);
+    __syncthreads();
+    uint32_t t = next_tile, phase = 0;
+    while (t < ntiles) {
+        const bool ok = mbar_wait(&bar, phase);
+        phase ^= 1u;
+        // also orders this tile's first exchange writes after the last tile's exchange reads
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0) {
+                atomicOr(ctl, 1u);
+                mbar_wait(&bar, phase ^ 1u);  // the copy that ran late: one more bounded wait
+            }
+            break;
+        }
+        cx<T> v[E];
+#pragma unroll
+        for (int s = 0; s < E; ++s) v[s] = stg[idx_e<LEN, E>(tq, s) * COLS + col];
+        __syncthreads();  // the staged tile has been read: refill it with the next tile
+        if (threadIdx.x == 0) {
+            const uint32_t nt = atomicAdd(ctl + 1, 1u);
+            if (nt < ntiles) {
+                mbar_arrive_expect_tx(&bar, kTileBytes);
+                tma_load_2d(stg, &wmap, (int)((nt % ncolt) * COLS), (int)((nt / ncolt) * LEN), &bar);
+            }
+            next_tile = nt;  // read by every thread after pack_pair_bits' barrier
+        }
+        const uint32_t pair = t / ncolt;
+        const uint64_t u0 = (uint64_t)(t % ncolt) * COLS, u = u0 + col;
+        const uint32_t ka = 2 * pair, kb = ka + 1;
+        const bool has_b = kb < nkeys;
+        twiddle_chain<T, true, E>(v, tw, (uint32_t)(tq * u), (uint32_t)((LEN / E) * u));
+        cta_fft<T, LEN, COLS, E, true>(sm, v, tq, col, tw);
+        const uint32_t popa = popc[ka], popb = has_b ? popc[kb] : 0u;
+        word_t *oa = reinterpret_cast<word_t *>(out + (uint64_t)ka * ostride);
+        word_t *ob = reinterpret_cast<word_t *>(out + (uint64_t)kb * ostride);
+        pack_pair_bits<T, LEN, COLS, E>(v, tq, col, S, u0, m, popa, popb, ka, kb, has_b, oa, ob, margin_bits, xkeys,
+                                        xstride);
+        t = next_tile;
+    }
+    if (threadIdx.x == 0 && atomicAdd(ctl + 2, 1u) == gridDim.x - 1) {
+        // every CTA has taken its last ticket: reset the counters for the next launch
+        atomicExch(ctl + 1, 0u);
+        atomicExch(ctl + 2, 0u);
     }
 }
 
@@ -616,9 +651,10 @@ __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
         }
         stage[a] = (uint64_t)wk | ((uint64_t)ws << 16) | ((uint64_t)inr << 32);
     }
-    ck = __reduce_add_sync(0xffffffffu, ck);
-    if ((threadIdx.x & 31) == 0 && ck) atomicAdd(popc + bd.id, ck);
-    __syncthreads();
+    uint32_t unused = 0u;
+    __shared__ uint32_t red[64];
+    cta_reduce2<false>(ck, unused, red);  // also publishes the staged rows
+    if (threadIdx.x == 0 && ck) atomicAdd(popc + bd.id, ck);
     cx<T> v[E];
 #pragma unroll
     for (int s = 0; s < E; ++s) {
@@ -667,15 +703,15 @@ __global__ void __launch_bounds__(2 * (LEN / E), min_blocks_inner(2 * (LEN / E))
 #pragma unroll
     for (int s = 0; s < E; ++s) y[s] = Arith<T>::mk((T)0, (T)0);
     for (int which = 0; which < (has2 ? 2 : 1); ++which) {
-        const cx<T> *w = Wf + (uint64_t)(which ? b2 : b1) * L + (uint64_t)row * LEN;
+        const cx<T> *wt = Wf + (uint64_t)(which ? b2 : b1) * L + (uint64_t)row * LEN + tq;
         cx<T> v[E];
         __syncthreads();  // previous use of the scratch is finished
         if constexpr (Plan<LEN, E>::RO == 1) {
 #pragma unroll
-            for (int s = 0; s < E; ++s) v[s] = w[idx_r0<LEN, E>(tq, s)];
+            for (int s = 0; s < E; ++s) v[s] = wt[idx_r0<LEN, E>(0, s)];
             cta_fft<T, LEN, 1, E, false>(sm, v, tq, 0, tw);
         } else {
-            cta_fft_fwd_odd<T, LEN, E>(sm, v, tq, tw, [&](uint32_t i) { return w[i]; });
+            cta_fft_fwd_odd<T, LEN, E>(sm, v, tq, tw, [&](uint32_t o) { return wt[o]; });
         }
         __syncthreads();
 #pragma unroll
@@ -702,16 +738,16 @@ __global__ void __launch_bounds__(2 * (LEN / E), min_blocks_inner(2 * (LEN / E))
         }
     }
     __syncthreads();
-    cx<T> *wo = Wi + (uint64_t)blockIdx.y * L + (uint64_t)row * LEN;
+    cx<T> *wot = Wi + (uint64_t)blockIdx.y * L + (uint64_t)row * LEN + tq;
     const bool store = !(self_paired && g == 1);  // a self-paired row is written once
     if constexpr (Plan<LEN, E>::RO == 1) {
         cta_fft<T, LEN, 1, E, true>(sm, y, tq, 0, tw);
         if (!store) return;
 #pragma unroll
-        for (int s = 0; s < E; ++s) wo[idx_r0<LEN, E>(tq, s)] = y[s];
+        for (int s = 0; s < E; ++s) wot[idx_r0<LEN, E>(0, s)] = y[s];
     } else {
-        cta_fft_inv_odd<T, LEN, E>(sm, y, tq, tw, [&](uint32_t i, cx<T> x) {
-            if (store) wo[i] = x;
+        cta_fft_inv_odd<T, LEN, E>(sm, y, tq, tw, [&](uint32_t o, cx<T> x) {
+            if (store) wot[o] = x;
         });
     }
 }
@@ -744,14 +780,14 @@ __global__ void __launch_bounds__(2 * (LEN / E), min_blocks_inner(2 * (LEN / E))
     const bool self_paired = rho == rho_m;
     cx<T> *sm = smem + g * SE;
     const cx<T> *sm_other = smem + (self_paired ? g : 1u - g) * SE;
-    cx<T> *w = W + (uint64_t)blockIdx.y * N + (uint64_t)row * LEN;
+    cx<T> *wt = W + (uint64_t)blockIdx.y * N + (uint64_t)row * LEN + tq;
     cx<T> v[E];
     if constexpr (Plan<LEN, E>::RO == 1) {
 #pragma unroll
-        for (int s = 0; s < E; ++s) v[s] = w[idx_r0<LEN, E>(tq, s)];
+        for (int s = 0; s < E; ++s) v[s] = wt[idx_r0<LEN, E>(0, s)];
         cta_fft<T, LEN, 1, E, false>(sm, v, tq, 0, tw);
     } else {
-        cta_fft_fwd_odd<T, LEN, E>(sm, v, tq, tw, [&](uint32_t i) { return w[i]; });
+        cta_fft_fwd_odd<T, LEN, E>(sm, v, tq, tw, [&](uint32_t o) { return wt[o]; });
     }
     __syncthreads();
 #pragma unroll
@@ -792,10 +828,10 @@ __global__ void __launch_bounds__(2 * (LEN / E), min_blocks_inner(2 * (LEN / E))
             cta_fft<T, LEN, 1, E, true>(sm, v, tq, 0, tw);
             if (!store) return;
 #pragma unroll
-            for (int s = 0; s < E; ++s) w[idx_r0<LEN, E>(tq, s)] = v[s];
+            for (int s = 0; s < E; ++s) wt[idx_r0<LEN, E>(0, s)] = v[s];
         } else {
-            cta_fft_inv_odd<T, LEN, E>(sm, v, tq, tw, [&](uint32_t i, cx<T> x) {
-                if (store) w[i] = x;
+            cta_fft_inv_odd<T, LEN, E>(sm, v, tq, tw, [&](uint32_t o, cx<T> x) {
+                if (store) wt[o] = x;
             });
         }
     }
@@ -850,9 +886,9 @@ __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
         }
     }
     uint32_t fa = __float_as_uint(margin_to_float(ma)), fb = __float_as_uint(margin_to_float(mb));
-    fa = __reduce_max_sync(0xffffffffu, fa);
-    fb = __reduce_max_sync(0xffffffffu, fb);
-    if (lane == 0) {
+    __shared__ uint32_t red[64];
+    cta_reduce2<true>(fa, fb, red);
+    if (threadIdx.x == 0) {
         atomicMax(margin_bits + ba_.id, fa);
         if (has_b) atomicMax(margin_bits + bb_.id, fb);
     }

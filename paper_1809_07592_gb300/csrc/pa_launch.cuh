@@ -122,24 +122,8 @@ cudaError_t launch_mid(int lgLEN, bool inverse, cx<T> *W, uint64_t L, uint32_t S
     });
 }
 
-// Shared memory of k_middle_pipe: two staging rows and the exchange buffer. The
-// pipelined kernel is used for rows of at least 3072 elements where that leaves
-// room for two CTAs per SM; on shorter rows the per-tile barriers and the extra
-// shared-memory traffic of the staging cost more than the hidden load latency
-// saves (measured: 1152-2560 slower or even, 3072-4608 faster by 6-13 %).
-template <typename T, int LEN>
-constexpr size_t pipe_smem_bytes() {
-    return 2 * (size_t)LEN * sizeof(cx<T>) + smem_bytes<T, LEN, 1>();
-}
-template <typename T, int LEN>
-constexpr bool pipe_ok() {
-    static_assert(pipe_smem_bytes<T, LEN>() == (3 * (size_t)LEN + LEN / 16 + 1) * sizeof(cx<T>), "pipe_fits formula");
-    return pipe_fits(LEN, sizeof(cx<T>));
-}
-
-// Persistent grid of k_middle_pipe: resident CTAs per SM (occupancy query) times the
-// SM count, each CTA owning an equal run of tiles. `cache` (one per kernel instance)
-// keeps the product per device.
+// Persistent grid of a kernel: resident CTAs per SM (occupancy query) times the SM
+// count. `cache` (one per kernel instance) keeps the product per device.
 template <typename K>
 cudaError_t persistent_ctas(K kern, int threads, size_t smem, int *cache, uint32_t *ctas) {
     int dev = 0;
@@ -161,28 +145,10 @@ cudaError_t persistent_ctas(K kern, int threads, size_t smem, int *cache, uint32
 
 template <typename T, int LEN>
 cudaError_t middle_at(int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pairs, TwTab<T> tw, cx<T> scale,
-                      cudaStream_t st, uint32_t *err, uint32_t expire_ns) {
+                      cudaStream_t st) {
     constexpr int E = Shape<T>::E;
     constexpr size_t sb = smem_bytes<T, LEN, 1>();
     dim3 grid((unsigned)(L / LEN), pairs);
-    if constexpr (pipe_ok<T, LEN>()) {
-        if (mode == 0 && err != nullptr) {
-            auto kern = k_middle_pipe<T, LEN, E>;
-            constexpr size_t pb = pipe_smem_bytes<T, LEN>();
-            cudaError_t e = set_smem(kern, pb);
-            if (e != cudaSuccess) return e;
-            static int cache[16] = {0};  // per (T, LEN): resident CTAs on each device
-            uint32_t ctas = 0;
-            e = persistent_ctas(kern, LEN / E, pb, cache, &ctas);
-            if (e != cudaSuccess) return e;
-            const uint64_t ntiles = (L / LEN) * pairs;
-            if (ntiles > 0xFFFFFFFFull) return cudaErrorInvalidValue;
-            const uint32_t per = (uint32_t)((ntiles + ctas - 1) / ctas);
-            const uint32_t nct = (uint32_t)((ntiles + per - 1) / per);
-            kern<<<nct, LEN / E, pb, st>>>(W, spec, L, pairs, per, tw, err, expire_ns);
-            return cudaGetLastError();
-        }
-    }
     if (mode == 0) {
         auto kern = k_middle<T, LEN, E, 0>;
         cudaError_t e = set_smem(kern, sb);
@@ -199,18 +165,18 @@ cudaError_t middle_at(int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pair
 
 template <typename T>
 cudaError_t launch_middle(int ro, int lg, int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pairs, TwTab<T> tw,
-                          cx<T> scale, cudaStream_t st, uint32_t *err, uint32_t expire_ns) {
+                          cx<T> scale, cudaStream_t st) {
     if (ro == 1) {
         return by_len<kMinLgMiddle, MaxLgMiddle<T>::v>(lg, [&](auto c) {
-            return middle_at<T, decltype(c)::value>(mode, W, spec, L, pairs, tw, scale, st, err, expire_ns);
+            return middle_at<T, decltype(c)::value>(mode, W, spec, L, pairs, tw, scale, st);
         });
     }
     if constexpr (std::is_same<T, Zp>::value) {
         return cudaErrorInvalidValue;  // the exact transform keeps power-of-two lengths
     } else {
-        if (ro == 3) return launch_middle_odd<T, 3>(lg, mode, W, spec, L, pairs, tw, scale, st, err, expire_ns);
-        if (ro == 5) return launch_middle_odd<T, 5>(lg, mode, W, spec, L, pairs, tw, scale, st, err, expire_ns);
-        if (ro == 9) return launch_middle_odd<T, 9>(lg, mode, W, spec, L, pairs, tw, scale, st, err, expire_ns);
+        if (ro == 3) return launch_middle_odd<T, 3>(lg, mode, W, spec, L, pairs, tw, scale, st);
+        if (ro == 5) return launch_middle_odd<T, 5>(lg, mode, W, spec, L, pairs, tw, scale, st);
+        if (ro == 9) return launch_middle_odd<T, 9>(lg, mode, W, spec, L, pairs, tw, scale, st);
         return cudaErrorInvalidValue;
     }
 }
@@ -218,32 +184,71 @@ cudaError_t launch_middle(int ro, int lg, int mode, cx<T> *W, cx<T> *spec, uint6
 // Odd innermost lengths RO * 2^lg, lg in [kMinLgOdd, kMaxLgOdd], where the CTA fits.
 template <typename T, int RO, int LG = kMinLgOdd>
 cudaError_t odd_middle_dispatch(int lg, int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pairs, TwTab<T> tw,
-                                cx<T> scale, cudaStream_t st, uint32_t *err, uint32_t expire_ns) {
+                                cx<T> scale, cudaStream_t st) {
     if constexpr (LG > kMaxLgOdd) {
         return cudaErrorInvalidValue;
     } else {
         if (lg == LG) {
             if constexpr (odd_inner_ok<T>(RO, LG, false)) {
-                return middle_at<T, RO * (1 << LG)>(mode, W, spec, L, pairs, tw, scale, st, err, expire_ns);
+                return middle_at<T, RO * (1 << LG)>(mode, W, spec, L, pairs, tw, scale, st);
             } else {
                 return cudaErrorInvalidValue;
             }
         }
-        return odd_middle_dispatch<T, RO, LG + 1>(lg, mode, W, spec, L, pairs, tw, scale, st, err, expire_ns);
+        return odd_middle_dispatch<T, RO, LG + 1>(lg, mode, W, spec, L, pairs, tw, scale, st);
     }
 }
 
 template <typename T, int RO>
 cudaError_t launch_middle_odd(int lg, int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pairs, TwTab<T> tw,
-                              cx<T> scale, cudaStream_t st, uint32_t *err, uint32_t expire_ns) {
-    return odd_middle_dispatch<T, RO>(lg, mode, W, spec, L, pairs, tw, scale, st, err, expire_ns);
+                              cx<T> scale, cudaStream_t st) {
+    return odd_middle_dispatch<T, RO>(lg, mode, W, spec, L, pairs, tw, scale, st);
+}
+
+// The TMA-staged persistent form of the level-1 inverse pass (k_inv_bits_tma): FP32 pair
+// form, LEN <= 256 (one tiled copy per tile), when the driver offers the tensor-map encoder.
+template <int LEN>
+cudaError_t inv_bits_tma_at(const float2 *W, uint64_t L, uint64_t m, uint32_t nkeys, const uint32_t *popc,
+                            uint32_t *margin_bits, uint64_t *out, uint64_t ostride, uint32_t pairs, TwTab<float> tw,
+                            cudaStream_t st, const uint64_t *xkeys, uint64_t xstride, uint32_t *ctl,
+                            uint32_t expire_ns, bool *done) {
+    *done = false;
+    constexpr int COLS = Shape<float>::COLS;
+    const uint64_t S = L / LEN;
+    CUtensorMap map;
+    if (!encode_tile_map(&map, W, S, (uint64_t)pairs * LEN, COLS, LEN)) return cudaSuccess;  // no encoder: plain kernel
+    auto kern = k_inv_bits_tma<LEN>;
+    // staged tile + exchange buffer + 128 bytes to align the tile for the tiled copy
+    constexpr size_t sb = (size_t)LEN * COLS * sizeof(float2) + smem_bytes<float, LEN, COLS>() + 128;
+    cudaError_t e = set_smem(kern, sb);
+    if (e != cudaSuccess) return e;
+    static int cache[16] = {0};  // resident CTAs on each device
+    uint32_t ctas = 0;
+    e = persistent_ctas(kern, LEN, sb, cache, &ctas);
+    if (e != cudaSuccess) return e;
+    const uint64_t ntiles = (S / COLS) * pairs;
+    if (ntiles > 0xFFFFFFFFull) return cudaErrorInvalidValue;
+    const uint32_t grid = (uint32_t)(ntiles < ctas ? ntiles : ctas);
+    kern<<<grid, LEN, sb, st>>>(map, L, m, nkeys, pairs, popc, margin_bits, out, ostride, tw, xkeys, xstride, ctl,
+                                expire_ns);
+    *done = true;
+    return cudaGetLastError();
 }
 
 template <typename T, int LEN, bool PACK>
 cudaError_t inv_bits_at(const cx<T> *W, uint64_t L, uint64_t m, uint32_t nkeys, const uint32_t *popc,
                         uint32_t *margin_bits, uint64_t *out, uint64_t ostride, uint32_t pairs, TwTab<T> tw,
-                        cudaStream_t st, const uint64_t *xkeys, uint64_t xstride) {
+                        cudaStream_t st, const uint64_t *xkeys, uint64_t xstride, uint32_t *ctl,
+                        uint32_t expire_ns) {
     constexpr int E = Shape<T>::E, COLS = Shape<T>::COLS;
+    if constexpr (std::is_same<T, float>::value && !PACK && LEN <= 256) {
+        if (ctl != nullptr) {
+            bool done = false;
+            cudaError_t e = inv_bits_tma_at<LEN>(W, L, m, nkeys, popc, margin_bits, out, ostride, pairs, tw, st, xkeys,
+                                                 xstride, ctl, expire_ns, &done);
+            if (e != cudaSuccess || done) return e;
+        }
+    }
     auto kern = k_inv_bits<T, LEN, COLS, E, PACK>;
     constexpr size_t sb = smem_bytes<T, LEN, COLS>();
     cudaError_t e = set_smem(kern, sb);
@@ -257,18 +262,18 @@ template <typename T>
 cudaError_t launch_inv_bits(int lgLEN, const cx<T> *W, uint64_t L, uint64_t m, uint32_t nkeys,
                             const uint32_t *popc, uint32_t *margin_bits, uint64_t *out, uint64_t ostride,
                             uint32_t pairs, TwTab<T> tw, cudaStream_t st, const uint64_t *xkeys,
-                            uint64_t xstride, bool pack) {
+                            uint64_t xstride, bool pack, uint32_t *ctl, uint32_t expire_ns) {
     return by_len<kMinLgStrided, kMaxLgStrided>(lgLEN, [&](auto c) {
         constexpr int LEN = decltype(c)::value;
         if constexpr (!std::is_same<T, Zp>::value) {
             if (pack)
                 return inv_bits_at<T, LEN, true>(W, L, m, nkeys, popc, margin_bits, out, ostride, pairs, tw, st,
-                                                 xkeys, xstride);
+                                                 xkeys, xstride, nullptr, 0u);
         } else {
             if (pack) return cudaErrorInvalidValue;
         }
         return inv_bits_at<T, LEN, false>(W, L, m, nkeys, popc, margin_bits, out, ostride, pairs, tw, st, xkeys,
-                                          xstride);
+                                          xstride, ctl, expire_ns);
     });
 }
 
@@ -281,10 +286,10 @@ cudaError_t launch_inv_bits(int lgLEN, const cx<T> *W, uint64_t L, uint64_t m, u
     template cudaError_t launch_mid<T>(int, bool, cx<T> *, uint64_t, uint32_t, uint32_t, TwTab<T>,               \
                                        cudaStream_t);                                                           \
     template cudaError_t launch_middle<T>(int, int, int, cx<T> *, cx<T> *, uint64_t, uint32_t, TwTab<T>, cx<T>,  \
-                                          cudaStream_t, uint32_t *, uint32_t);                                  \
+                                          cudaStream_t);                                                        \
     template cudaError_t launch_inv_bits<T>(int, const cx<T> *, uint64_t, uint64_t, uint32_t, const uint32_t *,  \
                                             uint32_t *, uint64_t *, uint64_t, uint32_t, TwTab<T>, cudaStream_t,  \
-                                            const uint64_t *, uint64_t, bool);
+                                            const uint64_t *, uint64_t, bool, uint32_t *, uint32_t);
 
 template <typename T>
 cudaError_t launch_fwd_keyseed(int lgLEN, const BlockDev *blocks, uint32_t nblocks, cx<T> *W, uint64_t L,
@@ -441,7 +446,7 @@ cudaError_t launch_middle_real(int ro, int lg, int mode, cx<T> *W, cx<T> *tabs, 
 // Odd innermost lengths of one (type, RO): the plain middle pass and the split pass.
 #define PA_INSTANTIATE_ODD(T, RO)                                                                               \
     template cudaError_t launch_middle_odd<T, RO>(int, int, cx<T> *, cx<T> *, uint64_t, uint32_t, TwTab<T>,     \
-                                                  cx<T>, cudaStream_t, uint32_t *, uint32_t);                   \
+                                                  cx<T>, cudaStream_t);                                         \
     template cudaError_t launch_middle_split_odd<T, RO>(int, const cx<T> *, cx<T> *, uint64_t, uint32_t,        \
                                                         uint32_t, uint32_t, TwTab<T>, cudaStream_t);            \
     template cudaError_t launch_middle_real_odd<T, RO>(int, int, cx<T> *, cx<T> *, uint64_t, uint32_t, uint32_t, \

@@ -9,6 +9,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "fft_core.cuh"
@@ -34,6 +35,10 @@ constexpr int kMinLgMiddle = 6;
 // Zero the per-key popcounts and margins of a batch (the level-1 forward pass accumulates the popcounts).
 cudaError_t launch_zero_keys(uint32_t nkeys, uint32_t *popc, uint32_t *margin_bits, cudaStream_t st);
 
+// Round x[0 .. count) in place to `bits` explicit significand bits (1 <= bits <= 22; other
+// values leave x as it is): the storage-precision study of pa_plan_set_storage_bits.
+cudaError_t launch_round_significand(float *x, uint64_t count, uint32_t bits, cudaStream_t st);
+
 // Level-1 forward pass of key pairs; also adds each key's popcount into popc[k]
 // (which must be zero beforehand: launch_zero_keys). The transform input is key
 // bits koff .. koff+n-1 (koff = m for the modified Toeplitz hash).
@@ -51,23 +56,13 @@ template <typename T>
 cudaError_t launch_mid(int lgLEN, bool inverse, cx<T> *W, uint64_t L, uint32_t S, uint32_t pairs, TwTab<T> tw,
                        cudaStream_t st);
 // Innermost pass of length ro * 2^lg. mode 0: the fused convolution step; mode 1:
-// the seed spectrum. With err != nullptr, mode 0 runs the persistent pipelined
-// kernel where its shared memory fits, and a copy wait that runs out of time sets
-// bit 0 of *err (device memory). expire_ns != 0 (test hook) makes that kernel issue
-// no copy and let its first wait run out after expire_ns.
+// the seed spectrum.
 template <typename T>
 cudaError_t launch_middle(int ro, int lg, int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pairs, TwTab<T> tw,
-                          cx<T> scale, cudaStream_t st, uint32_t *err = nullptr, uint32_t expire_ns = 0);
+                          cx<T> scale, cudaStream_t st);
 template <typename T, int RO>
 cudaError_t launch_middle_odd(int lg, int mode, cx<T> *W, cx<T> *spec, uint64_t L, uint32_t pairs, TwTab<T> tw,
-                              cx<T> scale, cudaStream_t st, uint32_t *err, uint32_t expire_ns);
-
-// Whether the fused convolution step of a row of `len` elements of `elem_bytes` bytes
-// runs as the persistent pipelined kernel (k_middle_pipe): rows of at least 3072
-// elements whose two staging rows and exchange buffer fit 112 KB of shared memory.
-constexpr bool pipe_fits(uint64_t len, uint64_t elem_bytes) {
-    return len >= 3072 && (2 * len + len + len / 16 + 1) * elem_bytes <= 112 * 1024;
-}
+                              cx<T> scale, cudaStream_t st);
 
 // Limits of the odd innermost lengths RO * 2^lg: a CTA has RO * 2^lg / E threads
 // (at most 1024, or 512 per row for the two-row split kernel).
@@ -78,11 +73,24 @@ constexpr bool odd_inner_ok(int ro, int lg, bool split) {
 }
 // Level-1 inverse pass with the bit output. With xkeys, output bit i of key k is
 // XORed with bit i of xkeys + k*xstride (the identity block of the modified hash).
+// With ctl != nullptr (three device words, zero before the first launch: error bits,
+// tile ticket, CTAs done), FP32 pairs with pass lengths up to 256 run the persistent
+// TMA-staged kernel; a copy wait there that runs out of time sets bit 0 of ctl[0].
+// expire_ns != 0 (test hook) makes that kernel copy nothing and let its wait run out.
 template <typename T>
 cudaError_t launch_inv_bits(int lgLEN, const cx<T> *W, uint64_t L, uint64_t m, uint32_t nkeys,
                             const uint32_t *popc, uint32_t *margin_bits, uint64_t *out, uint64_t ostride,
                             uint32_t pairs, TwTab<T> tw, cudaStream_t st, const uint64_t *xkeys = nullptr,
-                            uint64_t xstride = 0, bool pack = false);
+                            uint64_t xstride = 0, bool pack = false, uint32_t *ctl = nullptr,
+                            uint32_t expire_ns = 0);
+// Whether launch_inv_bits runs the TMA-staged kernel for this type and pass length.
+constexpr bool inv_bits_staged(uint64_t elem_bytes, int lgLEN) { return elem_bytes == 8 && lgLEN <= 8; }
+
+// Tiled-copy descriptor of a row-major array of rows x cols 8-byte elements at base, copied
+// in boxes of box_cols x box_rows (the cuTensorMapEncodeTiled encoder, resolved from the
+// driver at run time). false if the driver offers no encoder or rejects the layout.
+bool encode_tile_map(CUtensorMap *map, const void *base, uint64_t cols, uint64_t rows, uint32_t box_cols,
+                     uint32_t box_rows);
 
 // ---- uneven batch (complex arithmetic only: the Eq. 5-10 split needs conjugation) ----
 struct BlockDev;

@@ -545,3 +545,30 @@ def test_dv_qkd_step_on_two_streams(host):
                                       oracle.toeplitz_rows(n, m, c["seed"], c["keys"][33], rows),
                                       err_msg=f"(n, m) = ({n}, {m}), key 33")
         c["plan"].close()
+
+
+@pytest.mark.parametrize("modified", [False, True], ids=["standard", "modified"])
+@pytest.mark.parametrize("n,m", [(1 << 20, 104_857), (1 << 20, 1 << 18), (1_000_000, 500_000), (100_003, 40_001)])
+def test_staged_last_pass_bit_exact(n, m, modified):
+    """The TMA-staged last pass (pa_plan_set_staged) gives the same bits as the plain one on every
+    split; keys 0 and the last whole vs the oracle (odd key count: the lone key keeps its own form)."""
+    nk = 9
+    seed = inputs.bernoulli_bits(70 + m, 1, (n - 1) if modified else (n + m - 1))
+    keys = inputs.batch_keys(n, nk, base_seed=70 + m)
+    ow = (m + 63) // 64
+    splits = pa.pa_plan_splits(n - m if modified else n, m, pa.PA_FP32_GUARD) if not modified else [None]
+    for split in splits:
+        outs = []
+        for staged in (False, True):
+            p = pa.Plan(n, m, pa.PA_FP32_GUARD, split=split, modified=modified)
+            pa.pa_plan_set_staged(p.handle, staged)
+            p.set_seed(to_dev(seed)[0])
+            out, (marg, mode, esc) = p.hash(to_dev(keys), info=True)
+            torch.cuda.synchronize()
+            outs.append(to_host(out, ow))
+            assert esc == 0 and max(marg) < 0.05
+            p.close()
+        np.testing.assert_array_equal(outs[1], outs[0], err_msg=f"split {split}: staged vs plain")
+    ref = oracle.modified_hash if modified else oracle.toeplitz_hash
+    for k in (0, nk - 1):
+        np.testing.assert_array_equal(outs[1][k], ref(n, m, seed, keys[k]), err_msg=f"key {k}")

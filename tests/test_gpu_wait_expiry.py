@@ -1,8 +1,9 @@
-"""The device-side wait limit: a pipelined convolution launch whose copy wait runs out.
+"""The device-side wait limit: a staged last-pass launch whose copy wait runs out.
 
-The pipelined innermost kernel waits for its bulk copies with a time limit; a wait that
-runs out sets the plan's device error word and the kernel returns, so the GPU stays
-usable. pa_plan_expire_waits arms a test hook that makes the next launch issue no copy
+The staged last pass (pa_plan_set_staged; FP32 plans with a first pass of at most 256
+values) copies its input tiles with tiled asynchronous copies and waits for each with a
+time limit; a wait that runs out
+sets the plan's device error word and the kernel returns, so the GPU stays usable. pa_plan_expire_waits arms a test hook that makes the next launch issue no copy
 and wait on a barrier phase nothing completes (10 us), i.e. the wait certainly runs out
 with nothing in flight. The synchronising call must report PA_ETIMEOUT and clear the
 word; the next batch on the same plan must be bit-exact.
@@ -18,8 +19,7 @@ from tests.gpu_util import to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
-# n + m - 1 = 999,999: transform length 2^20; split 256 x 4096 puts 4096-value rows in the
-# pipelined innermost kernel
+# n + m - 1 = 999,999: transform length 2^20; split 256 x 4096 runs the staged last pass
 N, M, SPLIT = 800_000, 200_000, (256, 4096, 1)
 
 
@@ -33,6 +33,7 @@ def _lib():
 def _plan(seed):
     plan = pa.Plan(N, M, pa.PA_FP32_GUARD, split=SPLIT)
     assert tuple(plan.shape()) == (1 << 20,) + SPLIT
+    pa.pa_plan_set_staged(plan.handle, True)
     plan.set_seed(to_dev(seed)[0])
     return plan
 
@@ -64,9 +65,11 @@ def test_expired_wait_reports_timeout_then_plan_recovers(issue):
     plan.close()
 
 
-def test_expire_hook_rejected_without_pipelined_kernel():
-    plan = pa.Plan(N, M, pa.PA_FP64)  # FP64 rows never take the pipelined kernel
-    with pytest.raises(pa.PAError) as e:
-        pa.pa_plan_expire_waits(plan.handle, 1)
-    assert e.value.code == pa.PA_EUNSUPPORTED
-    plan.close()
+def test_expire_hook_rejected_without_staged_pass():
+    for dtype, staged in ((pa.PA_FP64, True), (pa.PA_FP32_GUARD, False)):  # FP64 plans never stage
+        plan = pa.Plan(N, M, dtype)
+        pa.pa_plan_set_staged(plan.handle, staged)
+        with pytest.raises(pa.PAError) as e:
+            pa.pa_plan_expire_waits(plan.handle, 1)
+        assert e.value.code == pa.PA_EUNSUPPORTED
+        plan.close()
