@@ -470,6 +470,37 @@ def measure_long_block(pa, inputs, torch, dev, reps=3):
     return res
 
 
+def measure_storage_precision(pa, inputs, torch, dev, bits_list=(23, 16, 13, 10, 7), lgs=range(16, 21), nkeys=8):
+    """The paper's Section 5 precision question, measured: the FP32 path with every value stored
+    between passes rounded to a narrower significand (pa_plan_set_storage_bits; 10 bits as in
+    FP16, 7 as in BF16), guard off, n = 2^16 .. 2^20, m = n/4, 8 keys: the largest rounding margin
+    max|w - rint(w)| over the keys. Above 0.25 the guard would send a key to FP64; near 0.5 the
+    rounding error has reached a whole unit and the parity is noise."""
+    table = {}
+    for lg in lgs:
+        n = 1 << lg
+        m = n // 4
+        seed = inputs.bernoulli_bits(lg, inputs.STREAM_SEED, n + m - 1)
+        keys = inputs.batch_keys(n, nkeys, base_seed=lg)
+        kw = keys.shape[1] + (keys.shape[1] & 1)
+        kb = np.zeros((nkeys, kw), np.uint64)
+        kb[:, : keys.shape[1]] = keys
+        dk = torch.from_numpy(kb.view(np.int64)).to(dev)
+        row = {}
+        for bits in bits_list:
+            plan = pa.Plan(n, m, pa.PA_FP32_GUARD)
+            pa.pa_plan_set_storage_bits(plan.handle, bits)
+            pa.pa_plan_set_guard(plan.handle, 1e9)
+            plan.set_seed(_dev_words(torch, seed, dev))
+            _, (marg, _mode, _esc) = plan.hash(dk, info=True)
+            torch.cuda.synchronize()
+            plan.close()
+            row[str(bits)] = max(marg)
+        table[str(n)] = row
+    return {"margin_max_by_n_and_significand_bits": table, "m_over_n": 0.25, "keys": nkeys,
+            "note": "guard off; 23 = FP32 storage as the product runs it"}
+
+
 def measure_modified(pa, inputs, torch, dev, steps=20):
     """The modified Toeplitz hash [I_m, T'] (Eq. 2-3) on the same DV-QKD batches (64 keys per (n, m),
     one seed of n-1 bits each): one step issues the six batches, then runs their guard steps."""
@@ -721,6 +752,7 @@ def run_ours(args):
         extra["cufft_comparison"] = measure_cufft_comparison(pa, inputs, torch, dev)
         extra["long_block_2p27"] = measure_long_block(pa, inputs, torch, dev)
         extra["modified_toeplitz"] = measure_modified(pa, inputs, torch, dev)
+        extra["storage_precision"] = measure_storage_precision(pa, inputs, torch, dev)
 
     if rank == 0:
         lat_sorted = sorted(lat_ms)

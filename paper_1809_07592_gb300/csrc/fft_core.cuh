@@ -293,6 +293,19 @@ __device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
         : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
     return d;
 }
+// d = a * b + c on both lanes of an f32x2 pair (one packed instruction).
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "mov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\t"
+        "mov.b64 {%0, %1}, rd;}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
 template <> struct Arith<float> : ComplexArith<float> {
     static __device__ __forceinline__ E add(E a, E b) { return f2_add(a, b); }
     static __device__ __forceinline__ E sub(E a, E b) { return f2_sub(a, b); }

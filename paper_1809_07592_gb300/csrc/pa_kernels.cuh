@@ -377,44 +377,73 @@ __device__ __forceinline__ float margin_to_float(double x) { return __double2flo
 
 // Round, mod 2 and pack the outputs of the level-1 inverse transform of one column
 // (pair form): v holds rows t1 = idx_r0(tq, s) of column u = u0 + col, the real part
-// belonging to key ka, the imaginary part to key kb (if has_b). Output bit i = t1*S + u
-// of a key is element i of the convolution window; bits >= m are written 0. Each key's
-// rounding margin max |w - rint(w)| over its m outputs goes to margin_bits (float bits,
+// belonging to key ka with ma_bits outputs, the imaginary part to key kb (if has_b) with
+// mb_bits outputs (the uneven batch pairs blocks of different lengths; a plan's pairs
+// have ma_bits = mb_bits = m). Output bit i = t1*S + u of a key is element i of the
+// convolution window; bits past the key's outputs are written 0. Each key's rounding
+// margin max |w - rint(w)| over its outputs goes to margin_bits[ka] / [kb] (float bits,
 // atomicMax; margins are >= 0, so integer order is float order). With xkeys, the bits
 // are XORed with key bits 0 .. m-1 (the identity block of the modified hash, Eq. 3).
 template <typename T, int LEN, int COLS, int E>
 __device__ __forceinline__ void pack_pair_bits(const cx<T> *v, uint32_t tq, uint32_t col, uint64_t S, uint64_t u0,
-                                               uint64_t m, uint32_t popa, uint32_t popb, uint32_t ka, uint32_t kb,
-                                               bool has_b, typename BitsWord<COLS>::type *oa,
+                                               uint64_t ma_bits, uint64_t mb_bits, uint32_t popa, uint32_t popb,
+                                               uint32_t ka, uint32_t kb, bool has_b,
+                                               typename BitsWord<COLS>::type *oa,
                                                typename BitsWord<COLS>::type *ob, uint32_t *margin_bits,
                                                const uint64_t *xkeys, uint64_t xstride) {
     using word_t = typename BitsWord<COLS>::type;
     const uint32_t lane = threadIdx.x & 31;
-    const uint64_t u = u0 + col;
-    const uint64_t nchunks = ((m + 63) >> 6) * (64 / COLS);
+    // 32-bit positions (t1*S + u < L <= 2^28). Rows at or past the end of the last output word
+    // are not decoded; the test uses the warp's first row of each slot (rows grow with tq, so
+    // the whole warp is past the end when its first row is), which keeps it warp-uniform: the
+    // ballots below need every lane.
+    const uint32_t S32 = (uint32_t)S, u032 = (uint32_t)u0;
+    const uint32_t ma32 = (uint32_t)ma_bits, mb32 = has_b ? (uint32_t)mb_bits : 0u;
+    const uint32_t mwa = (uint32_t)(((ma_bits + 63) >> 6) << 6), mwb = has_b ? (uint32_t)(((mb_bits + 63) >> 6) << 6) : 0u;
+    const uint32_t mw = mwa > mwb ? mwa : mwb;
+    const uint32_t tq0 = (threadIdx.x & ~31u) / COLS;  // the warp's first tq
     typename Enc<T>::M ma = 0, mb = 0;
+    [[maybe_unused]] float wa_max = 0.f, wb_max = 0.f;  // single precision: largest |w| of each key
+    [[maybe_unused]] const float2 half_p = make_float2(0.5f * (float)(popa & 3u), 0.5f * (float)(popb & 3u));
 #pragma unroll
     for (int s = 0; s < E; ++s) {
-        const uint64_t t1 = idx_r0<LEN, E>(tq, s);
-        const uint64_t i = t1 * S + u;
-        const uint64_t ci = (t1 * S + u0) / COLS;  // output chunk of this row's COLS bits
-        // rows past the last output word are not decoded (warp-uniform test: the ballot needs every lane)
-        if (!__any_sync(0xffffffffu, ci < nchunks)) continue;
+        const uint32_t t1 = idx_r0<LEN, E>(tq, s);
+        if (idx_r0<LEN, E>(tq0, s) * S32 + u032 >= mw) continue;
+        const uint32_t row0 = t1 * S32 + u032;  // output bit of this row's first column
+        const bool valid_a = row0 + col < ma32, valid_b = row0 + col < mb32;
         bool bit_a, bit_b;
-        Enc<T>::decode(v[s], popa, popb, i < m, bit_a, bit_b, ma, mb);
+        if constexpr (std::is_same<T, float>::value) {
+            // w = ((P mod 4) - r)/2 for both keys at once; rint by the 1.5*2^23 addition (exact for |w| < 2^22)
+            const float2 w = f2_fma(v[s], make_float2(-0.5f, -0.5f), half_p);
+            const float2 f = f2_add(w, make_float2(Magic<float>::v, Magic<float>::v));
+            const float2 d = f2_sub(w, f2_sub(f, make_float2(Magic<float>::v, Magic<float>::v)));
+            bit_a = valid_a && (__float_as_uint(f.x) & 1u);
+            bit_b = valid_b && (__float_as_uint(f.y) & 1u);
+            ma = fmaxf(ma, valid_a ? fabsf(d.x) : 0.f);
+            mb = fmaxf(mb, valid_b ? fabsf(d.y) : 0.f);
+            wa_max = fmaxf(wa_max, valid_a ? fabsf(w.x) : 0.f);
+            wb_max = fmaxf(wb_max, valid_b ? fabsf(w.y) : 0.f);
+        } else {
+            Enc<T>::decode2(v[s], popa, popb, valid_a, valid_b, bit_a, bit_b, ma, mb);
+        }
         const uint32_t ba = __ballot_sync(0xffffffffu, bit_a);
         const uint32_t bb = __ballot_sync(0xffffffffu, bit_b);
-        if (col == 0 && ci < nchunks) {
-            const uint32_t sh = lane;  // lane = group * COLS
+        if (col == 0) {
+            const uint32_t ci = row0 / COLS;  // output chunk of this row's COLS bits
             const uint32_t msk = (COLS == 32) ? 0xffffffffu : ((1u << COLS) - 1u);
-            uint32_t ya = (ba >> sh) & msk, yb = (bb >> sh) & msk;
+            uint32_t ya = (ba >> lane) & msk, yb = (bb >> lane) & msk;  // lane = group * COLS
             if (xkeys) {  // modified Toeplitz hash (Eq. 3): the identity block adds key bits 0 .. m-1
-                ya ^= aligned_bits<COLS>(xkeys + (uint64_t)ka * xstride, m, ci * COLS);
-                if (has_b) yb ^= aligned_bits<COLS>(xkeys + (uint64_t)kb * xstride, m, ci * COLS);
+                ya ^= aligned_bits<COLS>(xkeys + (uint64_t)ka * xstride, ma_bits, row0);
+                if (has_b) yb ^= aligned_bits<COLS>(xkeys + (uint64_t)kb * xstride, mb_bits, row0);
             }
-            oa[ci] = (word_t)ya;
-            if (has_b) ob[ci] = (word_t)yb;
+            if (row0 < mwa) oa[ci] = (word_t)ya;
+            if (row0 < mwb) ob[ci] = (word_t)yb;
         }
+    }
+    if constexpr (std::is_same<T, float>::value) {
+        // beyond the exact range of the rounding the parity is not resolvable: a margin of 1 escalates
+        if (wa_max >= Magic<float>::limit) ma = 1.f;
+        if (wb_max >= Magic<float>::limit) mb = 1.f;
     }
     uint32_t fa = __float_as_uint(margin_to_float(ma)), fb = __float_as_uint(margin_to_float(mb));
     __shared__ uint32_t red[64];
@@ -461,26 +490,47 @@ __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
     word_t *ob = reinterpret_cast<word_t *>(out + (uint64_t)kb * ostride);
     if constexpr (PACK) {
         typename Enc<T>::M ma = 0, mb = 0;
-        // chunk ci: the row's COLS elements t = t1*S + u0 + c, i.e. output bits 2*(t1*S + u0) .. +2*COLS
+        [[maybe_unused]] float w_max = 0.f;
+        [[maybe_unused]] const float half_p = 0.5f * (float)(popa & 3u);
+        // chunk ci: the row's COLS elements t = t1*S + u0 + c, i.e. output bits 2*(t1*S + u0) .. +2*COLS;
+        // 32-bit positions, and the warp-uniform skip of rows past the last output word as in pack_pair_bits
         using word2_t = typename BitsWord<2 * COLS>::type;
         word2_t *o2 = reinterpret_cast<word2_t *>(out + (uint64_t)ka * ostride);
-        const uint64_t nchunks2 = ((m + 63) >> 6) * (64 / (2 * COLS));
+        const uint32_t S32 = (uint32_t)S, u032 = (uint32_t)u0, m32 = (uint32_t)m;
+        const uint32_t mw = (uint32_t)(((m + 63) >> 6) << 6);  // output bits up to the end of the last word
+        const uint32_t tq0 = (threadIdx.x & ~31u) / COLS;
 #pragma unroll
         for (int s = 0; s < E; ++s) {
-            const uint64_t t1 = idx_r0<LEN, E>(tq, s);
-            const uint64_t t = t1 * S + u;
-            const uint64_t ci = (t1 * S + u0) / COLS;
-            if (!__any_sync(0xffffffffu, ci < nchunks2)) continue;
+            const uint32_t t1 = idx_r0<LEN, E>(tq, s);
+            if (2 * (idx_r0<LEN, E>(tq0, s) * S32 + u032) >= mw) continue;
+            const uint32_t row0 = t1 * S32 + u032;
+            const uint32_t t = row0 + col;
+            const bool ve = 2 * t < m32, vo = 2 * t + 1 < m32;
             bool bit_e, bit_o;
-            Enc<T>::decode2(v[s], popa, popa, 2 * t < m, 2 * t + 1 < m, bit_e, bit_o, ma, mb);
+            if constexpr (std::is_same<T, float>::value) {
+                const float2 w = f2_fma(v[s], make_float2(-0.5f, -0.5f), make_float2(half_p, half_p));
+                const float2 f = f2_add(w, make_float2(Magic<float>::v, Magic<float>::v));
+                const float2 d = f2_sub(w, f2_sub(f, make_float2(Magic<float>::v, Magic<float>::v)));
+                bit_e = ve && (__float_as_uint(f.x) & 1u);
+                bit_o = vo && (__float_as_uint(f.y) & 1u);
+                ma = fmaxf(ma, ve ? fabsf(d.x) : 0.f);
+                mb = fmaxf(mb, vo ? fabsf(d.y) : 0.f);
+                w_max = fmaxf(w_max, fmaxf(ve ? fabsf(w.x) : 0.f, vo ? fabsf(w.y) : 0.f));
+            } else {
+                Enc<T>::decode2(v[s], popa, popa, ve, vo, bit_e, bit_o, ma, mb);
+            }
             const uint32_t be = __ballot_sync(0xffffffffu, bit_e);
             const uint32_t bo = __ballot_sync(0xffffffffu, bit_o);
-            if (col == 0 && ci < nchunks2) {
+            if (col == 0 && 2 * row0 < mw) {
+                const uint32_t ci = row0 / COLS;
                 const uint32_t msk = (1u << COLS) - 1u;
                 uint32_t y = spread_bits((be >> lane) & msk) | (spread_bits((bo >> lane) & msk) << 1);
-                if (xkeys) y ^= bits_at(xkeys + (uint64_t)ka * xstride, m, 2 * (t1 * S + u0), 2 * COLS);
+                if (xkeys) y ^= bits_at(xkeys + (uint64_t)ka * xstride, m, 2 * (uint64_t)row0, 2 * COLS);
                 o2[ci] = (word2_t)y;
             }
+        }
+        if constexpr (std::is_same<T, float>::value) {
+            if (w_max >= Magic<float>::limit) ma = 1.f;  // parity not resolvable: escalate
         }
         uint32_t f = __float_as_uint(margin_to_float(ma > mb ? ma : mb)), unused = 0u;
         __shared__ uint32_t red[64];
@@ -488,7 +538,8 @@ __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
         if (threadIdx.x == 0) atomicMax(margin_bits + ka, f);
         return;
     }
-    pack_pair_bits<T, LEN, COLS, E>(v, tq, col, S, u0, m, popa, popb, ka, kb, has_b, oa, ob, margin_bits, xkeys, xstride);
+    pack_pair_bits<T, LEN, COLS, E>(v, tq, col, S, u0, m, m, popa, popb, ka, kb, has_b, oa, ob, margin_bits, xkeys,
+                                    xstride);
 }
 
 // The level-1 inverse pass of key pairs (FP32, pair form) as a persistent kernel whose
@@ -581,7 +632,7 @@ __global__ void __launch_bounds__(LEN, 768 / LEN)
         const uint32_t popa = popc[ka], popb = has_b ? popc[kb] : 0u;
         word_t *oa = reinterpret_cast<word_t *>(out + (uint64_t)ka * ostride);
         word_t *ob = reinterpret_cast<word_t *>(out + (uint64_t)kb * ostride);
-        pack_pair_bits<T, LEN, COLS, E>(v, tq, col, S, u0, m, popa, popb, ka, kb, has_b, oa, ob, margin_bits, xkeys,
+        pack_pair_bits<T, LEN, COLS, E>(v, tq, col, S, u0, m, m, popa, popb, ka, kb, has_b, oa, ob, margin_bits, xkeys,
                                         xstride);
         t = next_tile;
     }
@@ -865,33 +916,9 @@ __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
     const uint32_t popb = has_b ? popc[bb_.id] : 0u;
     word_t *oa = reinterpret_cast<word_t *>(ba_.out);
     word_t *ob = reinterpret_cast<word_t *>(bb_.out);
-    const uint64_t nca = ((ba_.m + 63) >> 6) * (64 / COLS), ncb = ((bb_.m + 63) >> 6) * (64 / COLS);
-    typename Enc<T>::M ma = 0, mb = 0;
-#pragma unroll
-    for (int s = 0; s < E; ++s) {
-        const uint64_t t1 = idx_r0<LEN, E>(tq, s);
-        const uint64_t i = t1 * S + u;
-        bool bit_a, bit_b, xa, xb;
-        typename Enc<T>::M da = 0, db = 0;
-        // decode each block with its own m (validity differs between the two blocks)
-        Enc<T>::decode(v[s], popa, popb, i < ba_.m, bit_a, xb, ma, da);
-        Enc<T>::decode(v[s], popa, popb, has_b && i < bb_.m, xa, bit_b, db, mb);
-        const uint32_t wa = __ballot_sync(0xffffffffu, bit_a);
-        const uint32_t wb = __ballot_sync(0xffffffffu, bit_b);
-        if (col == 0) {
-            const uint64_t ci = (t1 * S + u0) / COLS;
-            const uint32_t msk = (COLS == 32) ? 0xffffffffu : ((1u << COLS) - 1u);
-            if (ci < nca) oa[ci] = (word_t)((wa >> lane) & msk);
-            if (has_b && ci < ncb) ob[ci] = (word_t)((wb >> lane) & msk);
-        }
-    }
-    uint32_t fa = __float_as_uint(margin_to_float(ma)), fb = __float_as_uint(margin_to_float(mb));
-    __shared__ uint32_t red[64];
-    cta_reduce2<true>(fa, fb, red);
-    if (threadIdx.x == 0) {
-        atomicMax(margin_bits + ba_.id, fa);
-        if (has_b) atomicMax(margin_bits + bb_.id, fb);
-    }
+    // each block decoded with its own m: the real part is block 2p, the imaginary part block 2p+1
+    pack_pair_bits<T, LEN, COLS, E>(v, tq, col, S, u0, ba_.m, bb_.m, popa, popb, ba_.id, bb_.id, has_b, oa, ob,
+                                    margin_bits, nullptr, 0);
 }
 
 }  // namespace pa
