@@ -396,19 +396,26 @@ __device__ __forceinline__ void pack_pair_bits(const cx<T> *v, uint32_t tq, uint
     // 32-bit positions (t1*S + u < L <= 2^28). Rows at or past the end of the last output word
     // are not decoded; the test uses the warp's first row of each slot (rows grow with tq, so
     // the whole warp is past the end when its first row is), which keeps it warp-uniform: the
-    // ballots below need every lane.
+    // ballots below need every lane. The bound is taken once as a row count, and where a
+    // thread's rows grow with the slot (one radix-E last stage) the loop stops at the first
+    // slot past it.
     const uint32_t S32 = (uint32_t)S, u032 = (uint32_t)u0;
     const uint32_t ma32 = (uint32_t)ma_bits, mb32 = has_b ? (uint32_t)mb_bits : 0u;
     const uint32_t mwa = (uint32_t)(((ma_bits + 63) >> 6) << 6), mwb = has_b ? (uint32_t)(((mb_bits + 63) >> 6) << 6) : 0u;
     const uint32_t mw = mwa > mwb ? mwa : mwb;
     const uint32_t tq0 = (threadIdx.x & ~31u) / COLS;  // the warp's first tq
+    const uint32_t nrow = mw > u032 ? (mw - u032 + S32 - 1u) / S32 : 0u;  // rows t1 with t1*S + u0 < mw
     typename Enc<T>::M ma = 0, mb = 0;
     [[maybe_unused]] float wa_max = 0.f, wb_max = 0.f;  // single precision: largest |w| of each key
     [[maybe_unused]] const float2 half_p = make_float2(0.5f * (float)(popa & 3u), 0.5f * (float)(popb & 3u));
 #pragma unroll
     for (int s = 0; s < E; ++s) {
         const uint32_t t1 = idx_r0<LEN, E>(tq, s);
-        if (idx_r0<LEN, E>(tq0, s) * S32 + u032 >= mw) continue;
+        if constexpr (Plan<LEN, E>::r0 == E) {  // t1 = tq + s*TC: every later slot is past the bound too
+            if (idx_r0<LEN, E>(tq0, s) >= nrow) break;
+        } else {
+            if (idx_r0<LEN, E>(tq0, s) >= nrow) continue;
+        }
         const uint32_t row0 = t1 * S32 + u032;  // output bit of this row's first column
         const bool valid_a = row0 + col < ma32, valid_b = row0 + col < mb32;
         bool bit_a, bit_b;
@@ -499,10 +506,16 @@ __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
         const uint32_t S32 = (uint32_t)S, u032 = (uint32_t)u0, m32 = (uint32_t)m;
         const uint32_t mw = (uint32_t)(((m + 63) >> 6) << 6);  // output bits up to the end of the last word
         const uint32_t tq0 = (threadIdx.x & ~31u) / COLS;
+        const uint32_t half = mw >> 1;  // rows t1 with 2*(t1*S + u0) < mw: t1 < nrow
+        const uint32_t nrow = half > u032 ? (half - u032 + S32 - 1u) / S32 : 0u;
 #pragma unroll
         for (int s = 0; s < E; ++s) {
             const uint32_t t1 = idx_r0<LEN, E>(tq, s);
-            if (2 * (idx_r0<LEN, E>(tq0, s) * S32 + u032) >= mw) continue;
+            if constexpr (Plan<LEN, E>::r0 == E) {
+                if (idx_r0<LEN, E>(tq0, s) >= nrow) break;
+            } else {
+                if (idx_r0<LEN, E>(tq0, s) >= nrow) continue;
+            }
             const uint32_t row0 = t1 * S32 + u032;
             const uint32_t t = row0 + col;
             const bool ve = 2 * t < m32, vo = 2 * t + 1 < m32;
