@@ -45,7 +45,7 @@ static cudaError_t by_len(int lg, F &&f) {
 template <typename T, int LEN, bool PACK>
 cudaError_t fwd_keys_at(const uint64_t *keys, uint32_t nkeys, uint64_t kstride, uint64_t n, cx<T> *W, uint64_t L,
                         uint32_t pairs, TwTab<T> tw, uint32_t *popc, cudaStream_t st, uint64_t koff) {
-    constexpr int E = Shape<T>::E, COLS = Shape<T>::COLS;
+    constexpr int E = Shape<T>::E, COLS = strided_cols<T, LEN>();
     auto kern = k_fwd_keys<T, LEN, COLS, E, PACK>;
     constexpr size_t sb = smem_bytes<T, LEN, COLS>() + stage_bytes<T, LEN, COLS>();
     cudaError_t e = set_smem(kern, sb);
@@ -73,7 +73,7 @@ cudaError_t launch_fwd_keys(int lgLEN, const uint64_t *keys, uint32_t nkeys, uin
 template <typename T, int LEN, bool PACK>
 cudaError_t fwd_seed_at(const uint64_t *seed, uint64_t n, uint64_t m, cx<T> *W, uint64_t L, TwTab<T> tw,
                         cudaStream_t st) {
-    constexpr int E = Shape<T>::E, COLS = Shape<T>::COLS;
+    constexpr int E = Shape<T>::E, COLS = strided_cols<T, LEN>();
     auto kern = k_fwd_seed<T, LEN, COLS, E, PACK>;
     constexpr size_t sb = smem_bytes<T, LEN, COLS>();
     cudaError_t e = set_smem(kern, sb);
@@ -100,9 +100,10 @@ cudaError_t launch_fwd_seed(int lgLEN, const uint64_t *seed, uint64_t n, uint64_
 template <typename T>
 cudaError_t launch_mid(int lgLEN, bool inverse, cx<T> *W, uint64_t L, uint32_t S, uint32_t pairs, TwTab<T> tw,
                        cudaStream_t st) {
-    constexpr int E = Shape<T>::E, COLS = Shape<T>::COLS;
+    constexpr int E = Shape<T>::E;
     return by_len<kMinLgStrided, kMaxLgStrided>(lgLEN, [&](auto c) {
         constexpr int LEN = decltype(c)::value;
+        constexpr int COLS = strided_cols<T, LEN>();
         constexpr size_t sb = smem_bytes<T, LEN, COLS>();
         const uint64_t nblk = L / ((uint64_t)LEN * S);
         const uint32_t mult = (uint32_t)(L / ((uint64_t)LEN * S));
@@ -240,7 +241,7 @@ cudaError_t inv_bits_at(const cx<T> *W, uint64_t L, uint64_t m, uint32_t nkeys, 
                         uint32_t *margin_bits, uint64_t *out, uint64_t ostride, uint32_t pairs, TwTab<T> tw,
                         cudaStream_t st, const uint64_t *xkeys, uint64_t xstride, uint32_t *ctl,
                         uint32_t expire_ns) {
-    constexpr int E = Shape<T>::E, COLS = Shape<T>::COLS;
+    constexpr int E = Shape<T>::E, COLS = strided_cols<T, LEN>();
     if constexpr (std::is_same<T, float>::value && !PACK && LEN <= 256) {
         if (ctl != nullptr) {
             bool done = false;
@@ -294,9 +295,10 @@ cudaError_t launch_inv_bits(int lgLEN, const cx<T> *W, uint64_t L, uint64_t m, u
 template <typename T>
 cudaError_t launch_fwd_keyseed(int lgLEN, const BlockDev *blocks, uint32_t nblocks, cx<T> *W, uint64_t L,
                                TwTab<T> tw, uint32_t *popc, cudaStream_t st) {
-    constexpr int E = Shape<T>::E, COLS = Shape<T>::COLS;
+    constexpr int E = Shape<T>::E;
     return by_len<kMinLgStrided, kMaxLgStrided>(lgLEN, [&](auto c) {
         constexpr int LEN = decltype(c)::value;
+        constexpr int COLS = strided_cols<T, LEN>();
         auto kern = k_fwd_keyseed<T, LEN, COLS, E>;
         constexpr size_t sb = smem_bytes<T, LEN, COLS>() + 2 * stage_bytes<T, LEN, COLS>();  // 64-bit stage
         cudaError_t e = set_smem(kern, sb);
@@ -361,9 +363,10 @@ cudaError_t launch_middle_split_odd(int lg, const cx<T> *Wf, cx<T> *Wi, uint64_t
 template <typename T>
 cudaError_t launch_inv_bits_blocks(int lgLEN, const cx<T> *Wi, uint64_t L, const BlockDev *blocks, uint32_t nblocks,
                                    const uint32_t *popc, uint32_t *margin_bits, TwTab<T> tw, cudaStream_t st) {
-    constexpr int E = Shape<T>::E, COLS = Shape<T>::COLS;
+    constexpr int E = Shape<T>::E;
     return by_len<kMinLgStrided, kMaxLgStrided>(lgLEN, [&](auto c) {
         constexpr int LEN = decltype(c)::value;
+        constexpr int COLS = strided_cols<T, LEN>();
         auto kern = k_inv_bits_blocks<T, LEN, COLS, E>;
         constexpr size_t sb = smem_bytes<T, LEN, COLS>();
         cudaError_t e = set_smem(kern, sb);

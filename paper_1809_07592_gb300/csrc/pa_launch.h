@@ -23,6 +23,12 @@ template <typename T> struct Shape;
 template <> struct Shape<float> { static constexpr int E = 16, COLS = 16; };
 template <> struct Shape<double> { static constexpr int E = 8, COLS = 8; };
 template <> struct Shape<Zp> { static constexpr int E = 8, COLS = 8; };
+// Columns per CTA of a strided pass of length LEN: single precision takes 8 instead of 16 at
+// LEN = 1024 (512 threads, two CTAs per SM instead of one).
+template <typename T, int LEN>
+constexpr int strided_cols() {
+    return (sizeof(cx<T>) == 8 && LEN >= 1024) ? 8 : Shape<T>::COLS;
+}
 
 // Supported pass lengths (log2).
 constexpr int kMinLgStrided = 6, kMaxLgStrided = 10;
