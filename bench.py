@@ -434,6 +434,37 @@ def long_block_work(mode: str, L: int) -> tuple:
     return 2 * (N / 2) * math.log2(N) + N, "modmul"
 
 
+def long_block_passes(pa, plan, kd, out, stream, torch, n, m, block_ms, reps=5):
+    """Per-pass roofline of the FP32 long block (one key, half-length form, N = L/2 complex values,
+    W = 8 N bytes): each pass's live CUDA-event time (the library's per-launch events, in runs kept
+    apart from the timed ones) against the bytes that pass must move -- first pass W + n/8, each
+    middle strided pass 2 W, the fused innermost pass W in, the three seed tables (3 W) and W out,
+    the last pass W + m/8 -- and the block against the FP32 path's floor of 20 L + (n+m)/8 bytes."""
+    L = plan.shape()[0]
+    W = 8 * (L // 2)
+    need = {"fwd_keys": W + n / 8, "mid_fwd": 2 * W, "middle_conv": 5 * W, "mid_inv": 2 * W, "inv_bits": W + m / 8}
+    peak, kind = measured_peaks()
+    pa.pa_profile_enable(plan.handle, True)
+    pa.pa_profile_read(plan.handle, reset=True)
+    for _ in range(reps):
+        pa.pa_hash_batch(plan.handle, kd.view(1, -1), 1, kd.numel(), out, out.shape[1], stream)
+    torch.cuda.synchronize()
+    stats = pa.pa_profile_read(plan.handle, reset=True)
+    pa.pa_profile_enable(plan.handle, False)
+    passes = {}
+    for k, b in need.items():
+        cnt, tot = stats.get(k, (0, 0.0))
+        if cnt:
+            ms = tot / cnt
+            gbs = b / (ms * 1e-3) / 1e9
+            passes[k] = {"ms": ms, "bytes": b, "gbs": gbs, "frac": gbs / peak}
+    floor = 20 * L + (n + m) / 8
+    return {"per_pass": passes, "peak_gbs": peak, "peak_source": kind,
+            "block_floor_bytes": floor, "block_floor_frac": floor / (block_ms * 1e-3) / 1e9 / peak,
+            "block_design_bytes": sum(need.values()),
+            "block_design_frac": sum(need.values()) / (block_ms * 1e-3) / 1e9 / peak}
+
+
 def measure_long_block(pa, inputs, torch, dev, reps=3):
     """n = 2^27, m = 2^24 (transform length up to 2^28), one block, seed spectrum resident, per mode;
     the FP64 and NTT64 modes also against the measured FP64 FMA and modular-product peaks."""
@@ -459,6 +490,8 @@ def measure_long_block(pa, inputs, torch, dev, reps=3):
             ts.append(a.elapsed_time(b))
         ms = statistics.median(ts)
         res[name] = {"value": n / (ms * 1e-3) / 1e6, "unit": "Mbit/s", "ms": ms, "L": plan.shape()[0]}
+        if name == "fp32_guard":
+            res[name]["passes"] = long_block_passes(pa, plan, kd, out, stream, torch, n, m, ms)
         plan.close()
     fp64_gflops, zp_gmul = pa.pa_alu_peaks()
     for name, peak, unit in (("fp64", fp64_gflops * 1e9, "flop"), ("ntt64", zp_gmul * 1e9, "modmul")):
