@@ -434,6 +434,12 @@ def long_block_work(mode: str, L: int) -> tuple:
     return 2 * (N / 2) * math.log2(N) + N, "modmul"
 
 
+def long_block_pass_bytes(L: int, n: int, m: int) -> dict:
+    """Bytes each pass of a single-key (half-length, N = L/2, W = 8 N bytes) FP32 block must move."""
+    W = 8 * (L // 2)
+    return {"fwd_keys": W + n / 8, "mid_fwd": 2 * W, "middle_conv": 5 * W, "mid_inv": 2 * W, "inv_bits": W + m / 8}
+
+
 def long_block_passes(pa, plan, kd, out, stream, torch, n, m, block_ms, reps=5):
     """Per-pass roofline of the FP32 long block (one key, half-length form, N = L/2 complex values,
     W = 8 N bytes): each pass's live CUDA-event time (the library's per-launch events, in runs kept
@@ -441,8 +447,7 @@ def long_block_passes(pa, plan, kd, out, stream, torch, n, m, block_ms, reps=5):
     middle strided pass 2 W, the fused innermost pass W in, the three seed tables (3 W) and W out,
     the last pass W + m/8 -- and the block against the FP32 path's floor of 20 L + (n+m)/8 bytes."""
     L = plan.shape()[0]
-    W = 8 * (L // 2)
-    need = {"fwd_keys": W + n / 8, "mid_fwd": 2 * W, "middle_conv": 5 * W, "mid_inv": 2 * W, "inv_bits": W + m / 8}
+    need = long_block_pass_bytes(L, n, m)
     peak, kind = measured_peaks()
     pa.pa_profile_enable(plan.handle, True)
     pa.pa_profile_read(plan.handle, reset=True)
