@@ -39,11 +39,16 @@ __host__ __device__ constexpr int min_blocks(int threads) { return threads >= 10
 // The fused innermost passes ask for 512 resident threads per SM (<= 128
 // registers each). In single precision (8-byte elements) they ask for 768, at
 // most 8 CTAs: measured on the DV-QKD lengths, 17-31 % faster than 512 (more CTAs
-// overlap their barrier and load phases) with no spills; 896 or 1024 threads
-// per SM gain nothing further. The two-row split kernel keeps 512 (it spills above).
+// overlap their barrier and load phases) with no spills. Rows of 4608 and 5120
+// values (CTAs of 288 and 320 threads) ask for three CTAs (864 and 960 threads,
+// at most 75 and 68 registers, no spills): the pass ran 8.8 % faster on the
+// DV-QKD batches than with two; three CTAs of 384 threads (6144 values) spill and
+// were slower. The two-row split kernel keeps 512 (it spills above).
 __host__ __device__ constexpr int min_blocks_inner(int threads, int elem_bytes = 16) {
     return elem_bytes > 8 ? (threads >= 512 ? 1 : 512 / threads)
-                          : (threads >= 768 ? 1 : (768 / threads > 8 ? 8 : 768 / threads));
+                          : (threads >= 768 ? 1
+                                            : (threads == 288 || threads == 320) ? 3
+                                                                                  : (768 / threads > 8 ? 8 : 768 / threads));
 }
 
 // Rounding to the nearest integer (ties to even) by adding and subtracting
