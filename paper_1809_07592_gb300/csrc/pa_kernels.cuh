@@ -37,7 +37,7 @@ namespace pa {
 // CTAs overlap their load, transform and store phases.
 __host__ __device__ constexpr int min_blocks(int threads) { return threads >= 1024 ? 1 : (1024 / threads > 16 ? 16 : 1024 / threads); }
 // The fused innermost passes ask for 512 resident threads per SM (<= 128
-// registers each). In single precision (8-byte elements) they ask for 768, at
+// registers each; at most 16 CTAs). In single precision (8-byte elements) they ask for 768, at
 // most 8 CTAs: measured on the DV-QKD lengths, 17-31 % faster than 512 (more CTAs
 // overlap their barrier and load phases) with no spills. Rows of 4608 and 5120
 // values (CTAs of 288 and 320 threads) ask for three CTAs (864 and 960 threads,
@@ -45,7 +45,7 @@ __host__ __device__ constexpr int min_blocks(int threads) { return threads >= 10
 // DV-QKD batches than with two; three CTAs of 384 threads (6144 values) spill and
 // were slower. The two-row split kernel keeps 512 (it spills above).
 __host__ __device__ constexpr int min_blocks_inner(int threads, int elem_bytes = 16) {
-    return elem_bytes > 8 ? (threads >= 512 ? 1 : 512 / threads)
+    return elem_bytes > 8 ? (threads >= 512 ? 1 : (512 / threads > 16 ? 16 : 512 / threads))
                           : (threads >= 768 ? 1
                                             : (threads == 288 || threads == 320) ? 3
                                                                                   : (768 / threads > 8 ? 8 : 768 / threads));
@@ -354,20 +354,20 @@ __global__ void __launch_bounds__(LEN / E, min_blocks_inner(LEN / E, sizeof(cx<T
     } else {
         cta_fft_fwd_odd<T, LEN, E>(sm, v, tq, tw, [&](uint32_t o) { return wt[o]; });
     }
-    if (MODE == 1) {
+    if constexpr (MODE == 1) {
 #pragma unroll
         for (int s = 0; s < E; ++s) spt[idx_e<LEN, E>(0, s)] = Arith<T>::mul(v[s], scale);
-        return;
-    }
-#pragma unroll
-    for (int s = 0; s < E; ++s) v[s] = Arith<T>::mul(v[s], spt[idx_e<LEN, E>(0, s)]);
-    __syncthreads();  // the forward transform's last shared-memory reads are done
-    if constexpr (Plan<LEN, E>::RO == 1) {
-        cta_fft<T, LEN, 1, E, true>(sm, v, tq, 0, tw);
-#pragma unroll
-        for (int s = 0; s < E; ++s) wt[idx_r0<LEN, E>(0, s)] = v[s];
     } else {
-        cta_fft_inv_odd<T, LEN, E>(sm, v, tq, tw, [&](uint32_t o, cx<T> x) { wt[o] = x; });
+#pragma unroll
+        for (int s = 0; s < E; ++s) v[s] = Arith<T>::mul(v[s], spt[idx_e<LEN, E>(0, s)]);
+        __syncthreads();  // the forward transform's last shared-memory reads are done
+        if constexpr (Plan<LEN, E>::RO == 1) {
+            cta_fft<T, LEN, 1, E, true>(sm, v, tq, 0, tw);
+#pragma unroll
+            for (int s = 0; s < E; ++s) wt[idx_r0<LEN, E>(0, s)] = v[s];
+        } else {
+            cta_fft_inv_odd<T, LEN, E>(sm, v, tq, tw, [&](uint32_t o, cx<T> x) { wt[o] = x; });
+        }
     }
 }
 
@@ -916,7 +916,6 @@ __global__ void __launch_bounds__(COLS * LEN / E, min_blocks(COLS * LEN / E))
     cx<T> *sm = reinterpret_cast<cx<T> *>(smem_raw);
     using word_t = typename BitsWord<COLS>::type;
     const uint32_t col = threadIdx.x % COLS, tq = threadIdx.x / COLS;
-    const uint32_t lane = threadIdx.x & 31;
     const uint64_t S = L >> ilog2(LEN);
     const uint64_t u0 = (uint64_t)blockIdx.x * COLS;
     const uint64_t u = u0 + col;

@@ -27,7 +27,7 @@ template <> struct Shape<Zp> { static constexpr int E = 8, COLS = 8; };
 // LEN = 1024 (512 threads, two CTAs per SM instead of one).
 template <typename T, int LEN>
 constexpr int strided_cols() {
-    return (sizeof(cx<T>) == 8 && LEN >= 1024) ? 8 : Shape<T>::COLS;
+    return (std::is_same<T, float>::value && LEN >= 1024) ? 8 : Shape<T>::COLS;
 }
 
 // Supported pass lengths (log2).
