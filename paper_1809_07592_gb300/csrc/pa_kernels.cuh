@@ -39,16 +39,19 @@ __host__ __device__ constexpr int min_blocks(int threads) { return threads >= 10
 // The fused innermost passes ask for 512 resident threads per SM (<= 128
 // registers each; at most 16 CTAs). In single precision (8-byte elements) they ask for 768, at
 // most 8 CTAs: measured on the DV-QKD lengths, 17-31 % faster than 512 (more CTAs
-// overlap their barrier and load phases) with no spills. Rows of 4608 and 5120
-// values (CTAs of 288 and 320 threads) ask for three CTAs (864 and 960 threads,
-// at most 75 and 68 registers, no spills): the pass ran 8.8 % faster on the
-// DV-QKD batches than with two; three CTAs of 384 threads (6144 values) spill and
-// were slower. The two-row split kernel keeps 512 (it spills above).
+// overlap their barrier and load phases) with no spills. Rows of 5120 values
+// (CTAs of 320 threads) ask for three CTAs (960 threads, at most 68 registers)
+// and rows of 4608 (288 threads) for four (1152 threads, at most 56), both without
+// spills: the pass ran 8.8 % faster on the DV-QKD batches with three CTAs than with
+// two, and 0.6 % faster again with the fourth for 4608; four CTAs of 320 threads
+// and three of 384 (6144 values) spill and were slower. The two-row split kernel
+// keeps 512 (it spills above).
 __host__ __device__ constexpr int min_blocks_inner(int threads, int elem_bytes = 16) {
     return elem_bytes > 8 ? (threads >= 512 ? 1 : (512 / threads > 16 ? 16 : 512 / threads))
                           : (threads >= 768 ? 1
-                                            : (threads == 288 || threads == 320) ? 3
-                                                                                  : (768 / threads > 8 ? 8 : 768 / threads));
+                                            : threads == 288 ? 4
+                                            : threads == 320 ? 3
+                                                             : (768 / threads > 8 ? 8 : 768 / threads));
 }
 
 // Rounding to the nearest integer (ties to even) by adding and subtracting
